@@ -1,0 +1,183 @@
+"""FP64 CPU oracle for 3D Voronoi / power cells (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It shares no code with the CUDA path.
+
+The arithmetic lives in ``vd_oracle.c`` (plain C, FP64, OpenMP over cells);
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+What it computes is the cell of Eq. 1 (Sec. 3) clipped to a box, following
+the clipping procedure of App. B; see the header of ``vd_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STAT_NAMES = ("ambiguous", "degenerate", "orient_fail", "topo_fail", "clips", "tests", "empty", "facewalk_fail")
+
+ERRORS = {
+    -1: "invalid argument",
+    -2: "inconsistent cell topology",
+    -3: "neighbour capacity exceeded",
+    -4: "exact mode needs coordinates on the 2^-20 grid and weights on the 2^-40 grid",
+    -5: "out of memory",
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-fopenmp", "-std=gnu11", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            I32 = ctypes.c_int32
+            C = ctypes.c_int
+            lib.oracle_cells.argtypes = [P, P, I64, P, P, P, I64, C, C, P, P, I32, P, P, P, P, P, C]
+            lib.oracle_cells.restype = C
+            lib.oracle_grad.argtypes = [P, P, I64, P, P, P, I64, P, P, P, P, P, C]
+            lib.oracle_grad.restype = C
+            lib.oracle_certify.argtypes = [P, P, I64, P, P, P, I64, C, P, P, C]
+            lib.oracle_certify.restype = C
+            lib.oracle_cell_vertices.argtypes = [P, P, I64, P, P, I64, C, C, P, P, I32]
+            lib.oracle_cell_vertices.restype = C
+            lib.oracle_stat_count.restype = C
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prep(xyz, w, bbox):
+    xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+    w = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
+    if w is not None and w.shape[0] != xyz.shape[0]:
+        raise ValueError("weights must have one entry per site")
+    lo = np.ascontiguousarray(np.asarray(bbox[0], dtype=np.float32).reshape(3))
+    hi = np.ascontiguousarray(np.asarray(bbox[1], dtype=np.float32).reshape(3))
+    return xyz, w, lo, hi
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError(f"oracle error {rc}: {ERRORS.get(rc, 'unknown')}")
+
+
+def _threads(threads):
+    return int(threads) if threads else (os.cpu_count() or 1)
+
+
+def cells(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, mode="kd", exact=False,
+          threads=None, max_nbrs=512):
+    """Cells of the listed sites (all if ``cells`` is None).
+
+    Returns a dict: ``counts`` int32[m], ``nbrs`` list of ascending int32
+    arrays, ``offsets``/``indices`` (CSR), ``vol`` float64[m], ``cen``
+    float64[m,3], ``nverts``/``nfaces`` int32[m] and ``stats`` (dict).
+    """
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    n = xyz.shape[0]
+    idx = None if cells is None else np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+    m = n if idx is None else idx.shape[0]
+    counts = np.zeros(m, np.int32)
+    nbrs = np.full((m, max_nbrs), -1, np.int32)
+    vol = np.zeros(m, np.float64)
+    cen = np.zeros((m, 3), np.float64)
+    nv = np.zeros(m, np.int32)
+    nf = np.zeros(m, np.int32)
+    st = np.zeros(lib.oracle_stat_count(), np.int64)
+    rc = lib.oracle_cells(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(idx), m,
+                          0 if mode == "brute" else 1, 1 if exact else 0, _ptr(counts), _ptr(nbrs),
+                          max_nbrs, _ptr(vol), _ptr(cen), _ptr(nv), _ptr(nf), _ptr(st), _threads(threads))
+    _check(rc)
+    offsets = np.zeros(m + 1, np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    indices = np.concatenate([nbrs[q, : counts[q]] for q in range(m)]) if m else np.zeros(0, np.int32)
+    return {
+        "counts": counts,
+        "offsets": offsets,
+        "indices": indices.astype(np.int32),
+        "nbrs": [nbrs[q, : counts[q]].copy() for q in range(m)],
+        "vol": vol,
+        "cen": cen,
+        "nverts": nv,
+        "nfaces": nf,
+        "stats": dict(zip(STAT_NAMES, st.tolist())),
+    }
+
+
+def grad(xyz, w, bbox, c, d, cells=None, threads=None):
+    """Gradient of L = sum_i c_i V_i + d_i . g_i over the listed cells.
+
+    Returns ``(gp float64[n,3], gw float64[n], stats)``.
+    """
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    n = xyz.shape[0]
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(n))
+    d = np.ascontiguousarray(np.asarray(d, dtype=np.float64).reshape(n, 3))
+    idx = None if cells is None else np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+    m = n if idx is None else idx.shape[0]
+    gp = np.zeros((n, 3), np.float64)
+    gw = np.zeros(n, np.float64)
+    st = np.zeros(lib.oracle_stat_count(), np.int64)
+    rc = lib.oracle_grad(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(idx), m, _ptr(c), _ptr(d),
+                         _ptr(gp), _ptr(gw), _ptr(st), _threads(threads))
+    _check(rc)
+    return gp, gw, dict(zip(STAT_NAMES, st.tolist()))
+
+
+def certify(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, exact=False, threads=None):
+    """Per-cell count of (final vertex, other site) pairs violating the
+    empty-sphere condition pow(v, i) <= pow(v, m)."""
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    n = xyz.shape[0]
+    idx = None if cells is None else np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+    m = n if idx is None else idx.shape[0]
+    viol = np.zeros(m, np.int64)
+    st = np.zeros(lib.oracle_stat_count(), np.int64)
+    rc = lib.oracle_certify(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(idx), m, 1 if exact else 0,
+                            _ptr(viol), _ptr(st), _threads(threads))
+    _check(rc)
+    return viol, dict(zip(STAT_NAMES, st.tolist()))
+
+
+def cell_vertices(xyz, w, bbox, i, mode="kd", exact=False, cap=4096):
+    """Final vertices of one cell: (positions float64[k,3] in coordinates
+    relative to the site, defining sites int64[k,3]; box faces are -1-f)."""
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    pos = np.zeros((cap, 3), np.float64)
+    tri = np.zeros((cap, 3), np.int64)
+    k = lib.oracle_cell_vertices(_ptr(xyz), _ptr(w), xyz.shape[0], _ptr(lo), _ptr(hi), int(i),
+                                 0 if mode == "brute" else 1, 1 if exact else 0, _ptr(pos), _ptr(tri), cap)
+    if k < 0:
+        _check(k)
+    return pos[:k].copy(), tri[:k].copy()

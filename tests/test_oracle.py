@@ -1,0 +1,292 @@
+"""Pins for the FP64 CPU oracle against facts that do not come from the
+oracle itself: closed forms, library cross-checks (Qhull via scipy),
+exact-integer certificates, invariants of Eq. 1 and finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_06408_gb300 import workloads as W
+
+BOX = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def edges(nbrs):
+    return {(i, int(j)) for i, nb in enumerate(nbrs) for j in nb}
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_single_site_is_the_box():
+    x = np.array([[0.3, 0.6, 0.2]], np.float32)
+    box = ((-1.0, 0.0, 0.5 - 1.0), (2.0, 0.75, 1.5))
+    r = oracle.cells(x, bbox=box)
+    assert r["counts"][0] == 0
+    assert r["vol"][0] == pytest.approx(3.0 * 0.75 * 2.0, rel=1e-14)
+    np.testing.assert_allclose(r["cen"][0], [0.5, 0.375, 0.5], rtol=0, atol=1e-14)
+
+
+def test_two_site_closed_forms():
+    """Golden two-site cells (tests/golden/closed_forms.json, Sec. 3 Eq. 1)."""
+    with open(os.path.join(GOLDEN, "closed_forms.json")) as f:
+        g = json.load(f)
+    for case in g["cases"]:
+        x = np.array(case["xyz"], np.float32)
+        w = np.array(case["w"], np.float32)
+        r = oracle.cells(x, w, bbox=g["box"], mode="brute")
+        for i in range(2):
+            assert r["vol"][i] == pytest.approx(case["vol"][i], rel=1e-11, abs=1e-14)
+            if case["vol"][i] > 0 and case["vol"][1 - i] > 0:
+                assert list(r["nbrs"][i]) == [1 - i]
+        if case["kind"] == "slab":
+            for i in range(2):
+                if case["vol"][i] > 1e-9:
+                    np.testing.assert_allclose(r["cen"][i], case["cen"][i], rtol=0, atol=1e-11)
+
+
+def test_dominant_weight_owns_the_box():
+    x = W.uniform(200, 5)
+    w = np.zeros(200, np.float32)
+    w[17] = 10.0  # > squared box diagonal: pow(x, 17) < pow(x, j) everywhere
+    r = oracle.cells(x, w)
+    assert r["vol"][17] == pytest.approx(1.0, rel=1e-13)
+    assert r["counts"][17] == 0
+    others = np.arange(200) != 17
+    assert np.all(r["vol"][others] == 0.0) and np.all(r["counts"][others] == 0)
+    np.testing.assert_array_equal(r["cen"][others], x[others].astype(np.float64))
+    assert r["stats"]["empty"] == 199
+
+
+def test_bcc_truncated_octahedra():
+    """Interior cells of a (slightly jittered) BCC lattice with cube side a
+    are truncated octahedra: 14 neighbours, V = a^3/2, centroid = site."""
+    x, a = W.bcc_lattice(k=3, jitter=1e-7)
+    r = oracle.cells(x)
+    interior = np.all((x > 1.5 * a) & (x < 1.0 - 1.5 * a), axis=1)
+    assert interior.sum() > 50
+    assert np.all(r["counts"][interior] == 14)
+    assert np.all(r["nverts"][interior] == 24)
+    np.testing.assert_allclose(r["vol"][interior], a ** 3 / 2, rtol=1e-5)
+    np.testing.assert_allclose(r["cen"][interior], x[interior], rtol=0, atol=1e-6 * a)
+    # the 14 are the 8 body-diagonal and 6 axis lattice neighbours
+    for i in np.nonzero(interior)[0][:20]:
+        d = np.linalg.norm(x[r["nbrs"][i]] - x[i], axis=1) / a
+        assert np.sum(np.abs(d - np.sqrt(3) / 2) < 1e-3) == 8
+        assert np.sum(np.abs(d - 1.0) < 1e-3) == 6
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("kind", ["uniform", "mixture", "power"])
+def test_partition_invariants(kind):
+    n = 3000
+    if kind == "uniform":
+        x, w = W.uniform(n, 0), None
+    else:
+        x = W.mixture(n, 1)
+        w = W.power_weights(x, 2) if kind == "power" else None
+    r = oracle.cells(x, w)
+    assert r["stats"]["ambiguous"] == 0
+    assert r["stats"]["topo_fail"] == 0 and r["stats"]["facewalk_fail"] == 0
+    # cells partition the box: volumes and first moments add up
+    assert r["vol"].sum() == pytest.approx(1.0, rel=1e-12)
+    mom = (r["vol"][:, None] * r["cen"]).sum(0)
+    np.testing.assert_allclose(mom, [0.5, 0.5, 0.5], rtol=1e-12)
+    assert np.all(r["vol"] >= 0)
+    # adjacency is symmetric
+    E = edges(r["nbrs"])
+    assert all((j, i) in E for (i, j) in E)
+    assert len(E) % 2 == 0
+    # simple polytopes: every vertex has degree 3, so F = V/2 + 2
+    ne = r["nverts"] > 0
+    np.testing.assert_array_equal(r["nfaces"][ne], r["nverts"][ne] // 2 + 2)
+    assert np.all(r["nverts"][ne] % 2 == 0)
+    if kind == "power":
+        assert r["stats"]["empty"] > 0  # weights large enough to hide sites
+        empty = r["vol"] == 0
+        np.testing.assert_array_equal(r["cen"][empty], x[empty].astype(np.float64))
+
+
+def test_equal_weights_reproduce_voronoi():
+    x = W.mixture(2000, 3)
+    v = oracle.cells(x)
+    for c in (0.0, 0.25, -3.0):
+        p = oracle.cells(x, np.full(2000, c, np.float32))
+        assert all(np.array_equal(a, b) for a, b in zip(v["nbrs"], p["nbrs"]))
+        np.testing.assert_allclose(p["vol"], v["vol"], rtol=1e-9, atol=1e-15)
+
+
+def test_weight_shift_and_scaling_invariance():
+    x = W.uniform(1500, 9)
+    w = W.power_weights(x, 4)
+    base = oracle.cells(x, w)
+    # adding a constant (a power of two keeps float32 exact) changes nothing
+    shifted = oracle.cells(x, (w.astype(np.float64) + 0.5).astype(np.float32))
+    same = sum(np.array_equal(a, b) for a, b in zip(base["nbrs"], shifted["nbrs"]))
+    assert same == len(x)
+    # scaling positions by 2 and weights by 4 scales volumes by 8
+    scaled = oracle.cells(2 * x, 4 * w, bbox=((0, 0, 0), (2, 2, 2)))
+    assert all(np.array_equal(a, b) for a, b in zip(base["nbrs"], scaled["nbrs"]))
+    np.testing.assert_allclose(scaled["vol"], 8 * base["vol"], rtol=1e-10, atol=1e-18)
+
+
+def test_duplicates_and_outside_sites():
+    x = np.array([[0.2, 0.2, 0.2], [0.8, 0.5, 0.5], [0.2, 0.2, 0.2], [0.5, 0.9, 0.1]], np.float32)
+    r = oracle.cells(x)
+    assert r["vol"][2] == 0.0 and r["counts"][2] == 0  # equal weight: lower index wins
+    assert r["vol"][0] > 0
+    w = np.array([0.0, 0.0, 0.01, 0.0], np.float32)
+    r = oracle.cells(x, w)
+    assert r["vol"][0] == 0.0 and r["vol"][2] > 0  # larger weight wins
+    assert r["vol"].sum() == pytest.approx(1.0, rel=1e-12)
+    # a site outside the box still owns the part of the box nearest to it
+    y = np.array([[-0.25, 0.5, 0.5], [0.75, 0.5, 0.5]], np.float32)
+    r = oracle.cells(y)
+    assert r["vol"][0] == pytest.approx(0.25, rel=1e-13)  # bisector x = 0.25
+    assert list(r["nbrs"][0]) == [1]
+    y = np.array([[-0.5, 0.5, 0.5], [0.5, 0.5, 0.5]], np.float32)
+    assert oracle.cells(y)["vol"][0] == 0.0  # bisector on the box face
+
+
+# ---------------------------------------------------------------- brute force vs k-d stream
+
+def test_brute_equals_kd_on_uniform_10k():
+    x, _, box = W.config("uniform10k")
+    a = oracle.cells(x, bbox=box, mode="kd")
+    b = oracle.cells(x, bbox=box, mode="brute")
+    assert all(np.array_equal(p, q) for p, q in zip(a["nbrs"], b["nbrs"]))
+    np.testing.assert_allclose(a["vol"], b["vol"], rtol=1e-12)
+    assert a["stats"]["ambiguous"] == 0 and b["stats"]["ambiguous"] == 0
+
+
+def test_brute_equals_kd_on_weighted_subset():
+    x = W.mixture(6000, 12)
+    w = W.power_weights(x, 13)
+    a = oracle.cells(x, w, mode="kd")
+    b = oracle.cells(x, w, mode="brute")
+    assert all(np.array_equal(p, q) for p, q in zip(a["nbrs"], b["nbrs"]))
+    np.testing.assert_allclose(a["vol"], b["vol"], rtol=1e-11, atol=1e-18)
+
+
+# ---------------------------------------------------------------- exact arithmetic
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_exact_predicates_agree_and_certify(weighted):
+    x = W.snap_to_grid(W.mixture(1500, 21))
+    w = W.snap_weights(W.power_weights(x, 22)) if weighted else None
+    e = oracle.cells(x, w, exact=True)
+    f = oracle.cells(x, w, exact=False)
+    assert e["stats"]["degenerate"] == 0 and e["stats"]["orient_fail"] == 0
+    assert f["stats"]["ambiguous"] == 0
+    assert all(np.array_equal(p, q) for p, q in zip(e["nbrs"], f["nbrs"]))
+    # empty-sphere certificate in exact integer arithmetic: no final vertex
+    # of cell i has smaller power distance to any other site
+    viol, st = oracle.certify(x, w, exact=True)
+    assert viol.sum() == 0 and st["degenerate"] == 0
+
+
+# ---------------------------------------------------------------- library cross-checks
+
+def test_voronoi_neighbours_equal_qhull_delaunay_edges():
+    from scipy.spatial import Delaunay
+
+    x = W.uniform(400, 31)
+    big = ((-1e5,) * 3, (1e5,) * 3)
+    r = oracle.cells(x, bbox=big)
+    tri = Delaunay(x.astype(np.float64))
+    E = {(int(s[a]), int(s[b])) for s in tri.simplices for a in range(4) for b in range(4) if a != b}
+    assert edges(r["nbrs"]) == E
+
+
+def test_power_neighbours_equal_lifted_lower_hull_edges():
+    from scipy.spatial import ConvexHull
+
+    x = W.uniform(300, 32)
+    w = W.power_weights(x, 33, scale=0.5)
+    big = ((-1e4,) * 3, (1e4,) * 3)
+    r = oracle.cells(x, w, bbox=big)
+    p = x.astype(np.float64)
+    lift = np.concatenate([p, (p * p).sum(1, keepdims=True) - w.astype(np.float64)[:, None]], 1)
+    hull = ConvexHull(lift)
+    E = set()
+    for s, eq in zip(hull.simplices, hull.equations):
+        if eq[3] < 0:  # facet of the lower hull (outward normal points down)
+            E |= {(int(s[a]), int(s[b])) for a in range(4) for b in range(4) if a != b}
+    assert edges(r["nbrs"]) == E
+
+
+def test_poisson_voronoi_meijering_means():
+    """Mean faces 48 pi^2/35 + 2 = 15.54 and vertices 96 pi^2/35 = 27.07 per
+    interior Poisson-Voronoi cell (Meijering 1953)."""
+    x, _, box = W.config("uniform10k")
+    r = oracle.cells(x, bbox=box)
+    h = 2.5 * (1.0 / 10_000) ** (1 / 3)
+    interior = np.all((x > h) & (x < 1 - h), axis=1)
+    assert interior.sum() > 4000
+    assert r["nfaces"][interior].mean() == pytest.approx(48 * np.pi ** 2 / 35 + 2, abs=0.15)
+    assert r["nverts"][interior].mean() == pytest.approx(96 * np.pi ** 2 / 35, abs=0.3)
+
+
+# ---------------------------------------------------------------- gradients
+
+def _loss(x, w, c, d):
+    r = oracle.cells(x, w)
+    return float((c * r["vol"]).sum() + (d * r["cen"]).sum()), r["nbrs"]
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_gradient_matches_central_differences(weighted):
+    n = 120
+    x = W.uniform(n, 41)
+    w = W.power_weights(x, 42, scale=0.5) if weighted else None
+    c, d = W.loss_coefficients(n, 43)
+    gp, gw, st = oracle.grad(x, w, BOX, c, d)
+    rng = W.rng_for(44)
+    _, nb0 = _loss(x, w, c, d)
+    for k in rng.choice(n, 6, replace=False):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[k, a] = np.float32(x[k, a] + 2.0 ** -16)
+            xm[k, a] = np.float32(x[k, a] - 2.0 ** -16)
+            Lp, nbp = _loss(xp, w, c, d)
+            Lm, nbm = _loss(xm, w, c, d)
+            if not all(np.array_equal(u, v) for u, v in zip(nbp, nbm)):
+                continue  # combinatorics changed within +-h: outside the contract
+            fd = (Lp - Lm) / (float(xp[k, a]) - float(xm[k, a]))
+            assert fd == pytest.approx(gp[k, a], rel=2e-5, abs=2e-6)
+        if weighted:
+            wp, wm = w.copy(), w.copy()
+            hw = max(2.0 ** -30, 64 * float(np.spacing(w[k])))
+            wp[k] = np.float32(w[k] + hw)
+            wm[k] = np.float32(w[k] - hw)
+            fd = (_loss(x, wp, c, d)[0] - _loss(x, wm, c, d)[0]) / (float(wp[k]) - float(wm[k]))
+            assert fd == pytest.approx(gw[k], rel=2e-5, abs=2e-6)
+
+
+def test_total_volume_gradient_vanishes():
+    """sum_i V_i = vol(box) for every configuration, so its gradient is 0."""
+    n = 500
+    x = W.mixture(n, 51)
+    w = W.power_weights(x, 52)
+    gp, gw, _ = oracle.grad(x, w, BOX, np.ones(n), np.zeros((n, 3)))
+    r = oracle.cells(x, w)
+    scale = np.mean(r["vol"] ** (2.0 / 3.0))  # typical face area
+    assert np.abs(gp).max() < 1e-9 * scale
+    assert np.abs(gw).max() < 1e-9 * scale / np.median(r["vol"][r["vol"] > 0] ** (1 / 3))
+
+
+def test_gradient_subset_matches_full():
+    n = 400
+    x = W.uniform(n, 61)
+    c, d = W.loss_coefficients(n, 62)
+    gp, gw, _ = oracle.grad(x, None, BOX, c, d)
+    r = oracle.cells(x)
+    k = 123
+    sub = np.unique(np.concatenate([[k], r["nbrs"][k]])).astype(np.int64)
+    gps, gws, _ = oracle.grad(x, None, BOX, c, d, cells=sub)
+    np.testing.assert_allclose(gps[k], gp[k], rtol=1e-12, atol=1e-15)
+    assert gws[k] == pytest.approx(gw[k], rel=1e-12, abs=1e-15)
