@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the Voronoi / power-cell build on GB300.
+
+One step = one forward build of the whole point set (Morton keys, radix
+sort, LBVH, fused traversal + cull + clip kernel, CSR compaction) with the
+sites already resident in device memory; the reported value is Mcells/s.
+Forward+backward throughput, the end-to-end number through the C ABI from
+pinned host buffers, the roofline of the fused kernel and the FP64 CPU
+oracle on the host cores are reported in the same JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, same workload
+
+Under torchrun (N > 1) every rank builds its own independent point set
+(replicas: cells are independent, no collective on the data path) and the
+step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcells/s forward and forward+backward on 1 GB300 at oracle-exact neighbours; % of roofline"
+
+WORKLOADS = {
+    "mixture1M": "Voronoi of 1,000,000 sites from 64 anisotropic Gaussians (per-axis sigma log-uniform in "
+                 "[1e-3,1e-1]) + 10% uniform background, unit box, float32, seed 1",
+    "power1M": "power diagram of the mixture1M sites with w = r^2, r = 0.2 nn exp(N(0,1)), seed 2",
+    "uniform10k": "Voronoi of 10,000 uniform sites in the unit cube, seed 0",
+    "surfaces20M": "Voronoi of 20,000,000 sites in nested Gaussian shells (sigma 1e-2..1e-5) around 32 "
+                   "random surfaces + 1% background, seed 4",
+}
+
+# algorithmic FP32 work per counted event ("Roofline"):
+# one vertex/plane sign test = 3 FMA; one new vertex = three cross products,
+# a determinant, three 3-term numerators and a reciprocal (51 flop); one leaf
+# candidate = its plane and support test (30 flop); one BVH child = its
+# distance, radius and bound (40 flop).
+FLOP_VTEST, FLOP_NEWV, FLOP_CAND, FLOP_NODE = 6, 51, 30, 40
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="mixture1M", choices=sorted(WORKLOADS))
+    p.add_argument("--no-backward", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=300_000, help="cells in the oracle's timed sample")
+    p.add_argument("--config", default="", help="JSON dict of libvd config overrides")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name: str, rank: int):
+    from paper_2605_06408_gb300 import workloads as W
+
+    seed_shift = 1000 * rank  # independent point sets per rank
+    if name == "mixture1M":
+        return W.mixture(1_000_000, 1 + seed_shift), None, W.UNIT_BOX
+    if name == "power1M":
+        x = W.mixture(1_000_000, 1 + seed_shift)
+        return x, W.power_weights(x, 2 + seed_shift), W.UNIT_BOX
+    if name == "uniform10k":
+        return W.uniform(10_000, 0 + seed_shift), None, W.UNIT_BOX
+    if name == "surfaces20M":
+        return W.surfaces(20_000_000, 4 + seed_shift), None, W.UNIT_BOX
+    raise KeyError(name)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(x, w, box, sample: int, seed: int = 7):
+    """The FP64 oracle (k-d tree mode, OpenMP over all host cores) on a
+    seeded sample of the workload's cells. Returns (Mcells/s, cores, s)."""
+    import oracle
+    from paper_2605_06408_gb300 import workloads as W
+
+    rng = W.rng_for(seed)
+    m = min(sample, len(x))
+    cells = np.sort(rng.choice(len(x), m, replace=False))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.cells(x, w, box, cells=cells, threads=cores, max_nbrs=256)
+    dt = time.perf_counter() - t0
+    return m / dt / 1e6, cores, dt, m
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    x, w, box = make_workload(args.workload, 0)
+    sample = min(args.cpu_sample // 3, len(x))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(x, w, box, min(sample, 20_000))
+    rates, times = [], []
+    for k in range(args.steps):
+        r, cores, dt, m = cpu_oracle_rate(x, w, box, sample, seed=100 + k)
+        rates.append(r)
+        times.append(dt)
+    value = len(rates) * sample / sum(times) / 1e6
+    cb = {"value": value, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+          "sample": f"{sample} seeded cells of {args.workload} per step (FP64 k-d tree oracle, all host cores)"}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mcells/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": len(x)},
+           "cpu_baseline": cb, "e2e": {"value": value, "unit": "Mcells/s", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- GPU
+
+def fused_traffic_from_profiles(src_hash: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "cells_kernel_mixture1M.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if h and b and h.group(1) == src_hash:
+        return float(b.group(1))
+    return None
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    hsh = hashlib.sha256()
+    for f in ("vd_cells.cu", "vd_clip.cuh", "vd_internal.cuh"):
+        hsh.update(open(os.path.join(ROOT, "paper_2605_06408_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        dist = None
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2605_06408_gb300 import vd
+
+    x, w, box = make_workload(args.workload, rank)
+    n = len(x)
+    cfg = {"timing": 1}
+    if args.config:
+        cfg.update(json.loads(args.config))
+    ctx = vd.Context(local, cfg)
+    sites = torch.from_numpy(x).to(dev)
+    weights = None if w is None else torch.from_numpy(w).to(dev)
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up (also sizes the workspace and the neighbour buffer)
+    res = None
+    for _ in range(max(args.warmup, 1)):
+        res = ctx.build(sites, weights, box)
+    nnz = res.nnz
+    cap = nnz + 1024
+    st = ctx.status()
+
+    # algorithmic work of one build, from a separate counting run
+    cctx = vd.Context(local, dict(cfg, counters=1))
+    cctx.build(sites, weights, box)
+    cnt = cctx.status()
+    flop = (FLOP_VTEST * cnt["vertex_tests"] + FLOP_NEWV * cnt["new_vertices"] + FLOP_CAND * cnt["candidates"]
+            + FLOP_NODE * cnt["nodes"])
+    del cctx
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed forward steps
+    sampler = ClockSampler(local)
+    step_ms, cells_ms, launches = [], [], 0
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+        e1.record(stream)
+        t = ctx.timings()  # synchronises the stream
+        step_ms.append(e0.elapsed_time(e1))
+        cells_ms.append(t["cells_ms"])
+        launches += t["launches"]
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = statistics.mean(step_ms)
+
+    # ---- forward + backward
+    fb_ms = None
+    if not args.no_backward:
+        from paper_2605_06408_gb300 import workloads as W
+
+        c, d = W.loss_coefficients(n, 4)
+        gv = torch.from_numpy(c).float().to(dev)
+        gc = torch.from_numpy(d).float().to(dev)
+        ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+        ctx.backward(gv, gc, want_weights=weights is not None)
+        torch.cuda.synchronize()
+        fb = []
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+            ctx.backward(gv, gc, want_weights=weights is not None)
+            e1.record(stream)
+            e1.synchronize()
+            fb.append(e0.elapsed_time(e1))
+        barrier()
+        fb_ms = statistics.mean(fb)
+
+    # ---- end to end through the C ABI from pinned host buffers
+    h_sites = torch.from_numpy(x).pin_memory()
+    h_w = None if w is None else torch.from_numpy(w).pin_memory()
+    d_sites = torch.empty_like(sites)
+    d_w = None if w is None else torch.empty_like(weights)
+    h_off = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+    h_nb = torch.empty(nnz, dtype=torch.int32).pin_memory()
+    h_vol = torch.empty(n, dtype=torch.float32).pin_memory()
+    h_cen = torch.empty(n, 3, dtype=torch.float32).pin_memory()
+    e2e = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_sites.copy_(h_sites, non_blocking=True)
+        if d_w is not None:
+            d_w.copy_(h_w, non_blocking=True)
+        r = ctx.build(d_sites, d_w, box, nnz_capacity=cap, sync=False)
+        h_off.copy_(r.offsets, non_blocking=True)
+        h_nb.copy_(r.neighbors[:nnz], non_blocking=True)
+        h_vol.copy_(r.volume, non_blocking=True)
+        h_cen.copy_(r.centroid, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    barrier()
+    e2e_ms = statistics.mean(e2e)
+    h2d = 12 * n + (4 * n if w is not None else 0)
+    d2h = 4 * (n + 1) + 4 * nnz + 16 * n
+
+    def reduce_max(v):
+        if dist is None or v is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = reduce_max(ms)
+    fb_ms = reduce_max(fb_ms)
+    e2e_ms = reduce_max(e2e_ms)
+    total_cells = n * ws
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = 2070.0
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        sm_max = float(json.load(open(peaks_path)).get("sm_max_mhz", sm_max))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6  # FP32 lanes x FMA x clock
+    cms = statistics.mean(cells_ms)
+    achieved = flop / (cms * 1e-3)
+    src_hash = kernel_source_hash()
+    traffic = fused_traffic_from_profiles(src_hash)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, dt, m = cpu_oracle_rate(x, w, box, args.cpu_sample)
+        cpu = {"value": rate, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
+               "sample": f"{m} seeded cells of {args.workload} ({dt:.1f} s, FP64 k-d tree oracle, all host cores)"}
+
+    out = {
+        "metric": METRIC,
+        "value": total_cells / (ms * 1e-3) / 1e6,
+        "unit": "Mcells/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": n,
+                   "weighted": w is not None, "l2": "flushed between timed steps (256 MiB write)",
+                   "libvd": {k: v for k, v in ctx.config.items()}},
+        "fwd_bwd_mcells_s": None if fb_ms is None else total_cells / (fb_ms * 1e-3) / 1e6,
+        "fwd_bwd_ms_per_step": fb_ms,
+        "e2e": {"value": total_cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "kernel": "cells_kernel (fused traversal + cull + clip)",
+                     "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "flop_per_launch": flop, "cells_ms": cms},
+        "phase_ms": {k: v for k, v in ctx.timings().items() if k.endswith("_ms")},
+        "nnz": nnz,
+        "counters": {k: cnt[k] for k in ("candidates", "clips", "nodes", "vertex_tests", "new_vertices")},
+        "status": {k: st[k] for k in ("empty_cells", "overflow_cells", "failed_cells", "fp64_fallbacks",
+                                      "fp64_ambiguous")},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * vd.h -- C ABI of libvd: GB300-native (sm_103a) construction of 3D Voronoi
+ * and power-diagram cells by plane clipping.
+ *
+ * What a build computes (Sec. 3, Eq. 1): for every site i with position p_i
+ * and weight w_i, the cell
+ *     K_i = bbox ∩ { x : |x - p_i|^2 - w_i <= |x - p_j|^2 - w_j  for all j != i }
+ * (equal weights give the Voronoi diagram). Each cell starts as the box
+ * (App. B "Initialization", with the caller's box instead of the point-set
+ * bounds) and is clipped by the radical plane of every candidate neighbour
+ * (Sec. 4.1, App. B), with candidates from a best-first traversal of a
+ * Morton-sorted LBVH (Alg. 1, Sec. 4.3) culled by the directional bounds of
+ * Sec. 4.2.1 and the node bound of Sec. 4.2.2.
+ *
+ * Outputs per cell: the neighbour list (sites whose plane carries a face of
+ * positive area inside the box; box faces are not neighbours) in CSR form,
+ * sorted ascending within each row; the volume; the centroid. Empty cells
+ * (possible with weights) have no neighbours, volume 0 and centroid p_i.
+ *
+ * Conventions shared by every call:
+ *   - Return value: VD_OK (0) or a negative VD_ERR_* code for errors the host
+ *     can see at call time (bad arguments, CUDA launch/allocation failures).
+ *   - Asynchrony: work is enqueued on `stream` (a cudaStream_t passed as
+ *     void*); the calls do not synchronise the host. Errors found on the
+ *     device (non-finite input, neighbour capacity, cell overflow) are
+ *     written to the device status word of vd_out and to the context; read
+ *     them after synchronising, or with vd_get_status (which synchronises).
+ *   - Memory: input and output pointers are DEVICE pointers owned by the
+ *     caller and borrowed for the duration of the enqueued work. The context
+ *     owns its workspace (allocated on demand, grown when a larger problem
+ *     arrives) and keeps the sorted sites, the BVH and the neighbour lists of
+ *     the last forward build for vd_backward, until the next build.
+ *   - Graph capture: once the workspace has been sized for a problem (a first
+ *     call, or vd_reserve), vd_build / vd_build_batched / vd_backward enqueue
+ *     kernels and async memsets only and can be captured into a CUDA graph.
+ *   - Threads: one context must not be used by two host threads at once.
+ */
+#ifndef VD_H
+#define VD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define VD_OK 0
+#define VD_ERR_INVALID_ARG (-1)   /* n <= 0, NULL required pointer, lo >= hi, NaN/Inf */
+#define VD_ERR_CUDA (-2)          /* a CUDA call failed (allocation, launch)          */
+#define VD_ERR_CAPACITY (-3)      /* nnz > nnz_capacity; *nnz_out holds the size      */
+#define VD_ERR_CELL_OVERFLOW (-4) /* a cell exceeded the largest polytope capacity    */
+#define VD_ERR_NO_FORWARD (-5)    /* vd_backward without a matching forward build     */
+#define VD_ERR_TOO_LARGE (-6)     /* more sites than the index encoding supports      */
+
+/* ------------------------------------------------------------------ types */
+typedef struct vd_ctx vd_ctx;
+
+/* axis-aligned box, lo < hi componentwise */
+typedef struct {
+  float lo[3];
+  float hi[3];
+} vd_box;
+
+/* Output buffers, all DEVICE pointers owned by the caller. */
+typedef struct {
+  int32_t* offsets;     /* [n+1] CSR row offsets (offsets[0] = 0)                  */
+  int32_t* neighbors;   /* [nnz_capacity] neighbour indices, ascending per row;    */
+                        /*   for batched builds: indices local to the row's set    */
+  int64_t nnz_capacity; /* capacity of `neighbors` in elements                     */
+  int64_t* nnz_out;     /* device scalar: total neighbour count (always written)   */
+  float* volume;        /* [n] cell volumes (0 for empty cells)                    */
+  float* centroid;      /* [3n] cell centroids, xyz interleaved (p_i if empty)     */
+  int32_t* status;      /* device scalar: VD_OK or the first device-side error;    */
+                        /*   may be NULL                                           */
+} vd_out;
+
+/* Tuning knobs. vd_default_config fills the defaults; the autotuner of the
+ * Python layer overrides them per workload. */
+typedef struct {
+  int32_t leaf_size;       /* LBVH leaf size (1..32); default 16                     */
+  int32_t verts_per_lane;  /* polytope capacity per cell = 32 * this (2 or 4)        */
+  int32_t queue_per_lane;  /* best-first queue capacity per cell = 32 * this (1, 2)  */
+  int32_t cull_mode;       /* 0 directional (Sec. 4.2.1), 1 isotropic (single       */
+                           /*   radius, ablation), 2 none (every site is clipped)   */
+  int32_t traversal;       /* 0 best-first (Alg. 1), 1 depth-first (ablation)        */
+  int32_t warps_per_block; /* persistent kernel block size in warps (1..16)          */
+  int32_t blocks_per_sm;   /* persistent kernel grid = SMs * this (0 = occupancy)    */
+  int32_t counters;        /* 1: count tests, clips and nodes (small overhead)       */
+  int32_t timing;          /* 1: record CUDA events around each phase (vd_get_timings)*/
+} vd_config;
+
+/* Device-side results of the last call, read back by vd_get_status. */
+typedef struct {
+  int32_t error;              /* VD_OK or the first device-side error code          */
+  int32_t reserved;
+  int64_t nnz;                /* total neighbour count of the last build            */
+  int64_t empty_cells;        /* cells that ended empty                             */
+  int64_t overflow_cells;     /* cells re-run with the large-capacity kernel        */
+  int64_t failed_cells;       /* cells that overflowed even the large capacity      */
+  int64_t fp64_fallbacks;     /* FP32 predicates re-evaluated in FP64               */
+  int64_t fp64_ambiguous;     /* FP64 re-evaluations still inside their error bound */
+  int64_t candidates;         /* counters=1: candidate planes tested on vertices    */
+  int64_t clips;              /* counters=1: clips that removed vertices            */
+  int64_t nodes;              /* counters=1: BVH nodes tested                       */
+  int64_t vertex_tests;       /* counters=1: vertex-plane sign tests                */
+  int64_t new_vertices;       /* counters=1: vertices created                       */
+} vd_status;
+
+/* Per-phase device times of the last call, from CUDA events recorded on the
+ * call's stream when vd_config.timing = 1 (zeros otherwise). */
+typedef struct {
+  float pack_ms;      /* Morton keys, validation                              */
+  float sort_ms;      /* radix sort of (key, index)                           */
+  float bvh_ms;       /* packed sites, LBVH, refit, traversal records         */
+  float cells_ms;     /* fused traversal + cull + clip kernel                 */
+  float overflow_ms;  /* large-capacity pass for overflowed cells             */
+  float csr_ms;       /* scan + compaction                                    */
+  float backward_ms;  /* adjoint kernels (vd_backward)                        */
+  float total_ms;     /* whole call                                           */
+  int32_t launches;   /* kernels the call launched                            */
+  int32_t reserved;
+} vd_timings;
+
+/* ------------------------------------------------------------------ calls */
+
+/* Fill *cfg with the defaults. Returns VD_OK or VD_ERR_INVALID_ARG (NULL). */
+int vd_default_config(vd_config* cfg);
+
+/* Create a context on CUDA device `device` (the device becomes current for
+ * the calling thread). cfg may be NULL (defaults). The context allocates
+ * nothing until the first build or vd_reserve.
+ * Errors: VD_ERR_INVALID_ARG (NULL ctx, bad cfg), VD_ERR_CUDA. */
+int vd_create(vd_ctx** ctx, int device, const vd_config* cfg);
+
+/* Destroy a context and free its workspace. NULL is accepted. Does not
+ * synchronise streams: the caller must ensure its work has finished. */
+int vd_destroy(vd_ctx* ctx);
+
+/* Replace the context's configuration (same validation as vd_create). */
+int vd_set_config(vd_ctx* ctx, const vd_config* cfg);
+
+/* Pre-size the workspace for up to n sites (synchronous allocation), so
+ * that later builds of at most n sites allocate nothing and can be
+ * captured into a CUDA graph. */
+int vd_reserve(vd_ctx* ctx, int64_t n, int weighted);
+
+/* Bytes of device workspace a context needs for n sites. */
+size_t vd_workspace_bytes(int64_t n, int weighted);
+
+/* Forward build of one point set (Sec. 3 Eq. 1; pipeline of App. A).
+ *   sites_xyz : DEVICE float32 [3n], xyz interleaved.
+ *   weights   : DEVICE float32 [n] power weights, or NULL (Voronoi, w = 0).
+ *   n         : number of sites, 1 <= n <= 2^26.
+ *   bbox      : the box every cell starts from; sites outside it are allowed.
+ *   out       : caller-owned outputs (see vd_out); offsets/nnz_out/volume/
+ *               centroid are required, neighbors may be NULL only if
+ *               nnz_capacity == 0 (then only counts and geometry are made).
+ *   stream    : cudaStream_t as void* (NULL = legacy default stream).
+ * Device-side errors: VD_ERR_INVALID_ARG (non-finite coordinate or weight),
+ * VD_ERR_CAPACITY (neighbours not written, *nnz_out = required size; call
+ * vd_copy_neighbors with a larger buffer), VD_ERR_CELL_OVERFLOW. */
+int vd_build(vd_ctx* ctx, const float* sites_xyz, const float* weights, int64_t n, vd_box bbox,
+             const vd_out* out, void* stream);
+
+/* Copy the neighbour lists of the last build again, into a (larger)
+ * buffer, without rebuilding: out->offsets, out->neighbors,
+ * out->nnz_capacity, out->nnz_out and out->status are used. */
+int vd_copy_neighbors(vd_ctx* ctx, const vd_out* out, void* stream);
+
+/* Forward build of nsets independent point sets in one persistent launch
+ * (no paper counterpart: batching of the per-cell independence of Sec. 3).
+ *   sites_xyz   : DEVICE float32 [3N], the sets concatenated.
+ *   weights     : DEVICE float32 [N] or NULL.
+ *   set_offsets : HOST int64 [nsets+1], set s = sites [set_offsets[s],
+ *                 set_offsets[s+1]); set_offsets[0] = 0, non-decreasing.
+ *   boxes       : HOST [nsets] per-set boxes.
+ *   weighted    : HOST uint8 [nsets] (1 = power diagram using `weights`,
+ *                 0 = Voronoi) or NULL (all weighted iff weights != NULL).
+ *   nsets       : 1 <= nsets <= 1024.
+ * Offsets in `out` are global (N+1 entries); neighbour indices are local
+ * to the row's set. The host arrays are copied into the context before the
+ * call returns. */
+int vd_build_batched(vd_ctx* ctx, const float* sites_xyz, const float* weights, const int64_t* set_offsets,
+                     const vd_box* boxes, const uint8_t* weighted, int32_t nsets, const vd_out* out,
+                     void* stream);
+
+/* Adjoint of the last vd_build / vd_build_batched of this context (no paper
+ * counterpart): gradients of L = sum_i gv_i V_i + gc_i . g_i, with V_i the
+ * volume and g_i the centroid, with respect to site positions and weights,
+ * holding the cell combinatorics fixed (Reynolds transport over each
+ * site-site face; box faces are fixed).
+ *   grad_volume   : DEVICE float32 [n] or NULL (treated as 0).
+ *   grad_centroid : DEVICE float32 [3n] or NULL.
+ *   grad_sites    : DEVICE float32 [3n], overwritten.
+ *   grad_weights  : DEVICE float32 [n] or NULL, overwritten.
+ *   recompute     : must be 1: each cell is re-clipped from its stored
+ *                   neighbour list (no traversal).
+ * Errors: VD_ERR_NO_FORWARD if the context holds no forward build. */
+int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
+                float* grad_weights, int recompute, void* stream);
+
+/* Synchronise the context's last stream and return the phase times of the
+ * last call (no paper counterpart; a tracing aid). */
+int vd_get_timings(vd_ctx* ctx, vd_timings* t);
+
+/* Synchronise the context's last stream and copy its device-side status. */
+int vd_get_status(vd_ctx* ctx, vd_status* st);
+
+/* Static string for a VD_* code (never NULL). */
+const char* vd_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VD_H */

@@ -1,0 +1,558 @@
+// vd_api.cu -- the C ABI declared in include/vd.h: context, workspace and
+// the order of the kernels of one build (App. A pipeline: pack, BVH,
+// fused per-cell kernel; then CSR compaction). Everything is enqueued on
+// the caller's stream; nothing here synchronises the host except
+// workspace growth (cudaMalloc) and vd_get_status.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "vd_internal.cuh"
+
+using namespace vd;
+
+namespace {
+
+constexpr int kStride = 64;      // neighbour row stride of the register-resident pass
+constexpr int kStrideBig = 192;  // ... of the large-capacity pass
+constexpr int kHistEntries = 256 * 2 * kSortBlocksMax;
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t off[40];
+  int count = 0;
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    size_t o = total;
+    off[count++] = o;
+    total += align_up(bytes);
+    return o;
+  }
+};
+
+int64_t ovf_capacity(int64_t n) { return n / 16 > 4096 ? n / 16 : 4096; }
+
+}  // namespace
+
+struct vd_ctx {
+  int device = 0;
+  int num_sms = 0;
+  vd_config cfg;
+  // workspace
+  char* base = nullptr;
+  size_t bytes = 0;
+  int64_t cap_n = 0;
+  float4* sites = nullptr;
+  uint64_t* keys_a = nullptr;
+  uint64_t* keys_b = nullptr;
+  int* vals_a = nullptr;
+  int* vals_b = nullptr;
+  int* inv_perm = nullptr;
+  unsigned* hist = nullptr;
+  int* left = nullptr;
+  int* right = nullptr;
+  int* parent = nullptr;
+  int* visit = nullptr;
+  int2* range = nullptr;
+  float4* box_lo = nullptr;
+  float4* box_hi = nullptr;
+  float4* nodes = nullptr;
+  int* counts = nullptr;
+  int* scratch = nullptr;
+  int* scratch_big = nullptr;
+  int* ovf_list = nullptr;
+  int* ovf_slot = nullptr;
+  int* blist = nullptr;
+  long long* block_sums = nullptr;
+  int* work = nullptr;  // [4]
+  DevStatus* st = nullptr;
+  SetInfo* sets_dev = nullptr;
+  SetInfo* sets_host = nullptr;  // pinned staging
+  int ovf_cap = 0;
+  // last forward build
+  bool have_forward = false;
+  int last_n = 0;
+  int last_nsets = 0;
+  int set_shift = 63;
+  uint64_t* keys_sorted = nullptr;
+  int* perm = nullptr;
+  cudaStream_t last_stream = nullptr;
+  // phase timing (vd_config.timing)
+  cudaEvent_t ev[8] = {};
+  bool ev_made = false;
+  bool ev_valid = false;
+  bool ev_backward = false;
+  int launches = 0;
+};
+
+// events 0..6 bracket the phases: pack | sort | bvh | cells | overflow | csr
+static void mark(vd_ctx* ctx, int k, cudaStream_t s) {
+  if (!ctx->cfg.timing) return;
+  if (!ctx->ev_made) {
+    for (int q = 0; q < 8; q++) cudaEventCreate(&ctx->ev[q]);
+    ctx->ev_made = true;
+  }
+  cudaEventRecord(ctx->ev[k], s);
+}
+
+static int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return VD_OK;
+  return VD_ERR_CUDA;
+}
+
+static int check_config(const vd_config* c) {
+  if (c->leaf_size < 1 || c->leaf_size > kMaxLeaf) return VD_ERR_INVALID_ARG;
+  if (c->verts_per_lane != 2 && c->verts_per_lane != 4) return VD_ERR_INVALID_ARG;
+  if (c->queue_per_lane != 1 && c->queue_per_lane != 2) return VD_ERR_INVALID_ARG;
+  if (c->cull_mode < 0 || c->cull_mode > 2) return VD_ERR_INVALID_ARG;
+  if (c->traversal < 0 || c->traversal > 1) return VD_ERR_INVALID_ARG;
+  if (c->warps_per_block < 1 || c->warps_per_block > 16) return VD_ERR_INVALID_ARG;
+  if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64) return VD_ERR_INVALID_ARG;
+  if (c->counters < 0 || c->counters > 1 || c->timing < 0 || c->timing > 1) return VD_ERR_INVALID_ARG;
+  return VD_OK;
+}
+
+static int release(vd_ctx* ctx) {
+  if (ctx->base) cudaFree(ctx->base);
+  ctx->base = nullptr;
+  ctx->bytes = 0;
+  ctx->cap_n = 0;
+  ctx->have_forward = false;
+  return VD_OK;
+}
+
+static Layout make_layout(int64_t n) {
+  Layout L;
+  int64_t ovf = ovf_capacity(n);
+  int64_t nb = (n + 8191) / 8192 + 1;
+  L.add(sizeof(float4) * n);           // 0 sites
+  L.add(sizeof(uint64_t) * n);         // 1 keys_a
+  L.add(sizeof(uint64_t) * n);         // 2 keys_b
+  L.add(sizeof(int) * n);              // 3 vals_a
+  L.add(sizeof(int) * n);              // 4 vals_b
+  L.add(sizeof(int) * n);              // 5 inv_perm
+  L.add(sizeof(unsigned) * kHistEntries);  // 6 hist
+  L.add(sizeof(int) * n);              // 7 left
+  L.add(sizeof(int) * n);              // 8 right
+  L.add(sizeof(int) * 2 * n);          // 9 parent
+  L.add(sizeof(int) * n);              // 10 visit
+  L.add(sizeof(int2) * n);             // 11 range
+  L.add(sizeof(float4) * n);           // 12 box_lo
+  L.add(sizeof(float4) * n);           // 13 box_hi
+  L.add(sizeof(float4) * 4 * n);       // 14 nodes
+  L.add(sizeof(int) * n);              // 15 counts
+  L.add(sizeof(int) * (size_t)n * kStride);        // 16 scratch
+  L.add(sizeof(int) * (size_t)ovf * kStrideBig);   // 17 scratch_big
+  L.add(sizeof(int) * ovf);            // 18 ovf_list
+  L.add(sizeof(int) * n);              // 19 ovf_slot
+  L.add(sizeof(int) * ovf);            // 20 blist
+  L.add(sizeof(long long) * nb);       // 21 block_sums
+  L.add(sizeof(int) * 8);              // 22 work
+  L.add(sizeof(DevStatus));            // 23 status
+  L.add(sizeof(SetInfo) * kMaxSets);   // 24 sets
+  return L;
+}
+
+static int reserve(vd_ctx* ctx, int64_t n) {
+  if (n <= ctx->cap_n && ctx->base) return VD_OK;
+  int64_t want = n;
+  if (ctx->cap_n > 0 && want < ctx->cap_n + ctx->cap_n / 4) want = ctx->cap_n + ctx->cap_n / 4;
+  if (want > kMaxSites) want = kMaxSites;
+  if (want < 1024) want = 1024;
+  Layout L = make_layout(want);
+  release(ctx);
+  cudaError_t e = cudaMalloc(&ctx->base, L.total);
+  if (e != cudaSuccess) {
+    ctx->base = nullptr;
+    return VD_ERR_CUDA;
+  }
+  char* b = ctx->base;
+  ctx->bytes = L.total;
+  ctx->cap_n = want;
+  ctx->ovf_cap = (int)ovf_capacity(want);
+  ctx->sites = (float4*)(b + L.off[0]);
+  ctx->keys_a = (uint64_t*)(b + L.off[1]);
+  ctx->keys_b = (uint64_t*)(b + L.off[2]);
+  ctx->vals_a = (int*)(b + L.off[3]);
+  ctx->vals_b = (int*)(b + L.off[4]);
+  ctx->inv_perm = (int*)(b + L.off[5]);
+  ctx->hist = (unsigned*)(b + L.off[6]);
+  ctx->left = (int*)(b + L.off[7]);
+  ctx->right = (int*)(b + L.off[8]);
+  ctx->parent = (int*)(b + L.off[9]);
+  ctx->visit = (int*)(b + L.off[10]);
+  ctx->range = (int2*)(b + L.off[11]);
+  ctx->box_lo = (float4*)(b + L.off[12]);
+  ctx->box_hi = (float4*)(b + L.off[13]);
+  ctx->nodes = (float4*)(b + L.off[14]);
+  ctx->counts = (int*)(b + L.off[15]);
+  ctx->scratch = (int*)(b + L.off[16]);
+  ctx->scratch_big = (int*)(b + L.off[17]);
+  ctx->ovf_list = (int*)(b + L.off[18]);
+  ctx->ovf_slot = (int*)(b + L.off[19]);
+  ctx->blist = (int*)(b + L.off[20]);
+  ctx->block_sums = (long long*)(b + L.off[21]);
+  ctx->work = (int*)(b + L.off[22]);
+  ctx->st = (DevStatus*)(b + L.off[23]);
+  ctx->sets_dev = (SetInfo*)(b + L.off[24]);
+  return VD_OK;
+}
+
+static CellBuffers cell_buffers(vd_ctx* ctx) {
+  CellBuffers c;
+  std::memset(&c, 0, sizeof(c));
+  c.sites = ctx->sites;
+  c.perm = ctx->perm;
+  c.nodes = ctx->nodes;
+  c.keys = ctx->keys_sorted;
+  c.sets = ctx->sets_dev;
+  c.nsets = ctx->last_nsets;
+  c.set_shift = ctx->set_shift;
+  c.n = ctx->last_n;
+  c.counts = ctx->counts;
+  c.scratch = ctx->scratch;
+  c.stride = kStride;
+  c.scratch_big = ctx->scratch_big;
+  c.stride_big = kStrideBig;
+  c.ovf_list = ctx->ovf_list;
+  c.ovf_cap = ctx->ovf_cap;
+  c.ovf_slot = ctx->ovf_slot;
+  c.work = ctx->work;
+  c.st = ctx->st;
+  c.cfg = ctx->cfg;
+  return c;
+}
+
+static bool box_ok(const vd_box& b) {
+  for (int k = 0; k < 3; k++) {
+    if (!(b.lo[k] == b.lo[k]) || !(b.hi[k] == b.hi[k])) return false;
+    if (!(b.lo[k] < b.hi[k])) return false;
+    if (b.lo[k] < -3.0e38f || b.hi[k] > 3.0e38f) return false;
+  }
+  return true;
+}
+
+static bool out_ok(const vd_out* out) {
+  if (!out || !out->offsets || !out->nnz_out || !out->volume || !out->centroid) return false;
+  if (out->nnz_capacity < 0) return false;
+  if (!out->neighbors && out->nnz_capacity > 0) return false;
+  return true;
+}
+
+// The whole forward pipeline for nsets sets already staged in ctx->sets_host.
+static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int nsets, int set_shift,
+                       const vd_out* out, cudaStream_t s) {
+  cudaError_t e;
+  int rc = reserve(ctx, n);
+  if (rc) return rc;
+  ctx->have_forward = false;
+  ctx->ev_valid = false;
+  mark(ctx, 0, s);
+  e = cudaMemcpyAsync(ctx->sets_dev, ctx->sets_host, sizeof(SetInfo) * nsets, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s);
+  cudaMemsetAsync(ctx->work, 0, sizeof(int) * 8, s);
+  cudaMemsetAsync(ctx->ovf_slot, 0xff, sizeof(int) * (size_t)n, s);
+  cudaMemsetAsync(ctx->counts, 0, sizeof(int) * (size_t)n, s);
+  // 1. Morton keys (per-set quantisation) and input validation
+  e = launch_pack_keys(xyz, w, n, ctx->sets_dev, nsets, nullptr, set_shift, ctx->keys_a, ctx->vals_a, ctx->st, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  mark(ctx, 1, s);
+  // 2. radix sort of (key, index)
+  uint64_t* k0 = ctx->keys_a;
+  uint64_t* k1 = ctx->keys_b;
+  int* v0 = ctx->vals_a;
+  int* v1 = ctx->vals_b;
+  int bits = nsets > 1 ? 64 : 63;
+  e = radix_sort_pairs(k0, k1, v0, v1, ctx->hist, n, bits, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  ctx->keys_sorted = k0;
+  ctx->perm = v0;
+  mark(ctx, 2, s);
+  // 3. packed float4 sites in Morton order (App. A.1)
+  e = launch_gather_sites(xyz, w, ctx->perm, n, ctx->sets_dev, ctx->keys_sorted, set_shift, nsets, ctx->sites, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  e = launch_inverse_perm(ctx->perm, n, ctx->inv_perm, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  // 4. LBVH with per-node max weight (App. A.2)
+  BvhBuffers b;
+  b.keys = ctx->keys_sorted;
+  b.keys_alt = nullptr;
+  b.vals = nullptr;
+  b.vals_alt = nullptr;
+  b.hist = nullptr;
+  b.left = ctx->left;
+  b.right = ctx->right;
+  b.parent = ctx->parent;
+  b.range = ctx->range;
+  b.visit = ctx->visit;
+  b.box_lo = ctx->box_lo;
+  b.box_hi = ctx->box_hi;
+  b.nodes = ctx->nodes;
+  e = launch_build_bvh(ctx->keys_sorted, ctx->sites, n, ctx->cfg.leaf_size, b, ctx->sets_dev, nsets, ctx->st, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  // 5. fused traversal + cull + clip (Alg. 1, Sec. 4, App. B)
+  ctx->last_n = n;
+  ctx->last_nsets = nsets;
+  ctx->set_shift = set_shift;
+  CellBuffers c = cell_buffers(ctx);
+  c.vol = out->volume;
+  c.cen = out->centroid;
+  mark(ctx, 3, s);
+  e = launch_cells(c, ctx->num_sms, s, [&]() { mark(ctx, 4, s); });
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  mark(ctx, 5, s);
+  // 6. CSR
+  e = launch_csr(c, out->offsets, out->neighbors, out->nnz_capacity, out->nnz_out, ctx->block_sums, out->status,
+                 true, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  mark(ctx, 6, s);
+  ctx->have_forward = true;
+  ctx->last_stream = s;
+  ctx->ev_valid = ctx->cfg.timing != 0;
+  ctx->ev_backward = false;
+  int passes = (bits + 7) / 8;
+  ctx->launches = 1 + 3 * passes + 2 + (n >= 2 ? 4 : 1) + 2 + 3 + (out->neighbors && out->nnz_capacity > 0) + 1;
+  return VD_OK;
+}
+
+extern "C" {
+
+int vd_default_config(vd_config* cfg) {
+  if (!cfg) return VD_ERR_INVALID_ARG;
+  cfg->leaf_size = 16;
+  cfg->verts_per_lane = 2;
+  cfg->queue_per_lane = 2;
+  cfg->cull_mode = 0;
+  cfg->traversal = 0;
+  cfg->warps_per_block = 4;
+  cfg->blocks_per_sm = 0;
+  cfg->counters = 0;
+  cfg->timing = 0;
+  return VD_OK;
+}
+
+int vd_create(vd_ctx** out, int device, const vd_config* cfg) {
+  if (!out) return VD_ERR_INVALID_ARG;
+  *out = nullptr;
+  vd_config c;
+  vd_default_config(&c);
+  if (cfg) {
+    c = *cfg;
+    int rc = check_config(&c);
+    if (rc) return rc;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VD_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return VD_ERR_CUDA;
+  vd_ctx* ctx = new (std::nothrow) vd_ctx();
+  if (!ctx) return VD_ERR_CUDA;
+  ctx->device = device;
+  ctx->cfg = c;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return VD_ERR_CUDA;
+  }
+  if (cudaMallocHost(&ctx->sets_host, sizeof(SetInfo) * kMaxSets) != cudaSuccess) {
+    delete ctx;
+    return VD_ERR_CUDA;
+  }
+  *out = ctx;
+  return VD_OK;
+}
+
+int vd_destroy(vd_ctx* ctx) {
+  if (!ctx) return VD_OK;
+  cudaSetDevice(ctx->device);
+  release(ctx);
+  if (ctx->sets_host) cudaFreeHost(ctx->sets_host);
+  if (ctx->ev_made)
+    for (int q = 0; q < 8; q++) cudaEventDestroy(ctx->ev[q]);
+  delete ctx;
+  return VD_OK;
+}
+
+int vd_set_config(vd_ctx* ctx, const vd_config* cfg) {
+  if (!ctx || !cfg) return VD_ERR_INVALID_ARG;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  ctx->cfg = *cfg;
+  return VD_OK;
+}
+
+int vd_reserve(vd_ctx* ctx, int64_t n, int /*weighted*/) {
+  if (!ctx || n <= 0) return VD_ERR_INVALID_ARG;
+  if (n > kMaxSites) return VD_ERR_TOO_LARGE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  return reserve(ctx, n);
+}
+
+size_t vd_workspace_bytes(int64_t n, int /*weighted*/) {
+  if (n <= 0) return 0;
+  if (n < 1024) n = 1024;
+  return make_layout(n).total;
+}
+
+int vd_build(vd_ctx* ctx, const float* xyz, const float* weights, int64_t n, vd_box bbox, const vd_out* out,
+             void* stream) {
+  if (!ctx || !xyz || n <= 0 || !box_ok(bbox) || !out_ok(out)) return VD_ERR_INVALID_ARG;
+  if (n > kMaxSites) return VD_ERR_TOO_LARGE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  SetInfo& S = ctx->sets_host[0];
+  for (int k = 0; k < 3; k++) {
+    S.lo[k] = bbox.lo[k];
+    S.hi[k] = bbox.hi[k];
+  }
+  S.first = 0;
+  S.count = (int)n;
+  S.root = 0;
+  S.weighted = weights ? 1 : 0;
+  return run_forward(ctx, xyz, weights, (int)n, 1, 63, out, (cudaStream_t)stream);
+}
+
+int vd_copy_neighbors(vd_ctx* ctx, const vd_out* out, void* stream) {
+  if (!ctx || !out || !out->offsets || !out->nnz_out || out->nnz_capacity < 0) return VD_ERR_INVALID_ARG;
+  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  CellBuffers c = cell_buffers(ctx);
+  // clear a previous capacity error, keep any other
+  cudaError_t e = launch_csr(c, out->offsets, out->neighbors, out->nnz_capacity, out->nnz_out, ctx->block_sums,
+                             out->status, true, s);
+  ctx->last_stream = s;
+  return cuda_fail(e);
+}
+
+int vd_build_batched(vd_ctx* ctx, const float* xyz, const float* weights, const int64_t* set_offsets,
+                     const vd_box* boxes, const uint8_t* weighted, int32_t nsets, const vd_out* out, void* stream) {
+  if (!ctx || !xyz || !set_offsets || !boxes || nsets < 1 || nsets > kMaxSets || !out_ok(out))
+    return VD_ERR_INVALID_ARG;
+  if (set_offsets[0] != 0) return VD_ERR_INVALID_ARG;
+  for (int s = 0; s < nsets; s++) {
+    if (set_offsets[s + 1] < set_offsets[s]) return VD_ERR_INVALID_ARG;
+    if (!box_ok(boxes[s])) return VD_ERR_INVALID_ARG;
+  }
+  int64_t n = set_offsets[nsets];
+  if (n <= 0) return VD_ERR_INVALID_ARG;
+  if (n > kMaxSites) return VD_ERR_TOO_LARGE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  for (int s = 0; s < nsets; s++) {
+    SetInfo& S = ctx->sets_host[s];
+    for (int k = 0; k < 3; k++) {
+      S.lo[k] = boxes[s].lo[k];
+      S.hi[k] = boxes[s].hi[k];
+    }
+    S.first = (int)set_offsets[s];
+    S.count = (int)(set_offsets[s + 1] - set_offsets[s]);
+    S.root = 0;
+    S.weighted = weights ? (weighted ? (weighted[s] ? 1 : 0) : 1) : 0;
+  }
+  // Morton codes of 18 bits per axis below a 10-bit set id
+  return run_forward(ctx, xyz, weights, (int)n, nsets, 54, out, (cudaStream_t)stream);
+}
+
+int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
+                float* grad_weights, int recompute, void* stream) {
+  if (!ctx || !grad_sites || recompute != 1) return VD_ERR_INVALID_ARG;
+  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int n = ctx->last_n;
+  cudaMemsetAsync(grad_sites, 0, sizeof(float) * 3 * (size_t)n, s);
+  if (grad_weights) cudaMemsetAsync(grad_weights, 0, sizeof(float) * (size_t)n, s);
+  cudaMemsetAsync(ctx->work + 2, 0, sizeof(int) * 3, s);
+  BackBuffers b;
+  b.c = cell_buffers(ctx);
+  b.inv_perm = ctx->inv_perm;
+  b.gvol = grad_volume;
+  b.gcen = grad_centroid;
+  b.gp = grad_sites;
+  b.gw = grad_weights;
+  b.list = ctx->blist;
+  b.list_count = ctx->work + 4;
+  b.list_cap = ctx->ovf_cap;
+  b.work = ctx->work + 2;
+  ctx->ev_valid = false;
+  mark(ctx, 0, s);
+  cudaError_t e = launch_backward(b, ctx->num_sms, s);
+  mark(ctx, 6, s);
+  ctx->last_stream = s;
+  ctx->ev_valid = ctx->cfg.timing != 0;
+  ctx->ev_backward = true;
+  ctx->launches = 2;
+  return cuda_fail(e);
+}
+
+int vd_get_timings(vd_ctx* ctx, vd_timings* t) {
+  if (!ctx || !t) return VD_ERR_INVALID_ARG;
+  std::memset(t, 0, sizeof(*t));
+  t->launches = ctx->launches;
+  if (!ctx->ev_valid) return VD_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return VD_ERR_CUDA;
+  auto el = [&](int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+    return ms;
+  };
+  if (ctx->ev_backward) {
+    t->backward_ms = el(0, 6);
+    t->total_ms = t->backward_ms;
+  } else {
+    t->pack_ms = el(0, 1);
+    t->sort_ms = el(1, 2);
+    t->bvh_ms = el(2, 3);
+    t->cells_ms = el(3, 4);
+    t->overflow_ms = el(4, 5);
+    t->csr_ms = el(5, 6);
+    t->total_ms = el(0, 6);
+  }
+  return VD_OK;
+}
+
+int vd_get_status(vd_ctx* ctx, vd_status* st) {
+  if (!ctx || !st) return VD_ERR_INVALID_ARG;
+  std::memset(st, 0, sizeof(*st));
+  if (!ctx->st) return VD_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return VD_ERR_CUDA;
+  DevStatus d;
+  if (cudaMemcpy(&d, ctx->st, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return VD_ERR_CUDA;
+  st->error = d.error;
+  st->nnz = d.nnz;
+  st->empty_cells = d.empty_cells;
+  st->overflow_cells = d.overflow_cells;
+  st->failed_cells = d.failed_cells;
+  st->fp64_fallbacks = d.fp64_fallbacks;
+  st->fp64_ambiguous = d.fp64_ambiguous;
+  st->candidates = d.candidates;
+  st->clips = d.clips;
+  st->nodes = d.nodes;
+  st->vertex_tests = d.vertex_tests;
+  st->new_vertices = d.new_vertices;
+  return VD_OK;
+}
+
+const char* vd_error_string(int code) {
+  switch (code) {
+    case VD_OK:
+      return "ok";
+    case VD_ERR_INVALID_ARG:
+      return "invalid argument (n, pointers, box, or a non-finite coordinate or weight)";
+    case VD_ERR_CUDA:
+      return "CUDA call failed";
+    case VD_ERR_CAPACITY:
+      return "neighbour capacity too small; *nnz_out holds the required size";
+    case VD_ERR_CELL_OVERFLOW:
+      return "a cell exceeded the largest polytope capacity";
+    case VD_ERR_NO_FORWARD:
+      return "no forward build in this context";
+    case VD_ERR_TOO_LARGE:
+      return "too many sites or neighbours for the index encoding";
+    default:
+      return "unknown error";
+  }
+}
+
+}  // extern "C"

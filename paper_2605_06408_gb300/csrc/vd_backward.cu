@@ -1,0 +1,273 @@
+// vd_backward.cu -- adjoint of the forward build (no counterpart in the
+// paper, which constructs the diagram only).
+//
+// L = sum_i gv_i V_i + gc_i . g_i (V = volume, g = centroid). With the cell
+// combinatorics held fixed, only site-site faces move: on face F_ij of cell
+// i (distance D = |p_j - p_i|, n = p_j - p_i, local coordinates x~ = x - p_i)
+// the boundary's normal speed is (n - x~).dp_j / D, x~.dp_i / D, dw_i / 2D
+// and -dw_j / 2D (differentiate |x-p_i|^2 - w_i - |x-p_j|^2 + w_j = 0 and
+// divide by its gradient 2D). Reynolds transport then gives, with
+// A = area, Am = int x~ dA, S = int x~ x~^T dA over F_ij,
+//   dL_i = a' dV + b . dM~,   b = gc_i / V_i,   a' = gv_i - b . g~_i,
+//   dV/dp_j = (A n - Am)/D, dV/dp_i = Am/D, dV/dw_i = -dV/dw_j = A/2D,
+//   dM~/dp_j = (Am n^T - S)/D, dM~/dp_i = S/D, dM~/dw_i = -dM~/dw_j = Am/2D,
+// where M~ = int x~ dV and g~ = M~/V. Each cell is re-clipped from its
+// stored neighbour list (no traversal), its faces integrated by the same
+// fan tetrahedra as the forward pass, and the face terms scatter-added.
+#include "vd_clip.cuh"
+
+namespace vd {
+
+template <int VPL, int PCAP>
+struct BackSmem {
+  WarpSmem<VPL, PCAP> w;
+  float acc[PCAP][10];  // per face: A, int y (3), int y y^T (6), y = x~ - c
+};
+
+template <int VPL, int PCAP, int QPL>
+__device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si, Counters& ct) {
+  using C = Cell<VPL, PCAP, QPL>;
+  constexpr int NPW = C::NPW;
+  const CellBuffers& P = B.c;
+  WarpSmem<VPL, PCAP>& S = SM.w;
+  const unsigned lane = lane_id();
+  C c;
+  c.me = P.sites[si];
+  const int orig_i = P.perm[si];
+  const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
+  const SetInfo& SI = P.sets[set];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c.lo[k] = SI.lo[k];
+    c.hi[k] = SI.hi[k];
+  }
+  const int cnt = P.counts[orig_i];
+  if (cnt <= 0) return true;  // empty cell (or no site faces): no moving face
+  init_cell(c, S);
+  const int slot = P.ovf_slot[orig_i];
+  const int* row = slot >= 0 ? P.scratch_big + (size_t)slot * P.stride_big : P.scratch + (size_t)orig_i * P.stride;
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    int t = c0 + (int)lane;
+    bool keep = t < cnt;
+    int j = 0;
+    PlaneT<float> H;
+    H.nx = H.ny = H.nz = H.b = H.e = 0.f;
+    float dkey = INFINITY;
+    if (keep) {
+      j = B.inv_perm[row[t] + SI.first];
+      float4 q = P.sites[j];
+      H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+      dkey = H.b;
+    }
+    uint32_t km = __ballot_sync(FULL, keep);
+    while (km) {
+      uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
+      uint32_t mn = __reduce_min_sync(FULL, key);
+      int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
+      PlaneT<float> Hb;
+      Hb.nx = __shfl_sync(FULL, H.nx, src);
+      Hb.ny = __shfl_sync(FULL, H.ny, src);
+      Hb.nz = __shfl_sync(FULL, H.nz, src);
+      Hb.b = __shfl_sync(FULL, H.b, src);
+      Hb.e = __shfl_sync(FULL, H.e, src);
+      int hj = __shfl_sync(FULL, j, src);
+      if ((int)lane == src) keep = false;
+      km &= ~(1u << src);
+      int rc = clip_cell(c, S, Hb, hj, P.sites, ct, false);
+      if (rc == CLIP_OVERFLOW) return false;
+      if (rc == CLIP_EMPTY) return true;
+    }
+  }
+  float sx, sy, sz;
+  uint32_t alive[NPW];
+  const int nv = gather_vertices(c, S, sx, sy, sz, alive);
+  const float cx = sx / nv, cy = sy / nv, cz = sz / nv;
+  for (int f = (int)lane; f < PCAP; f += 32)
+#pragma unroll
+    for (int q = 0; q < 10; q++) SM.acc[f][q] = 0.f;
+  __syncwarp();
+  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
+  for (int it = (int)lane; it < 3 * nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t T = S.nvt[t];
+    uint32_t U = T | (T << 24);
+    uint32_t xy = (U >> (8 * rho)) & 0xffffu;
+    uint32_t fx = xy & 255u, fy = xy >> 8;
+    uint32_t q = fy | (fx << 8);
+    int u = 0;
+    while (u < nv && !tri_has_pair(S.nvt[u], q)) u++;
+    if (u >= nv) continue;
+    float4 pf = S.pl[fy];
+    float hgt = fmaf(pf.x, cx, fmaf(pf.y, cy, fmaf(pf.z, cz, -pf.w)));
+    float g[3] = {-hgt * pf.x, -hgt * pf.y, -hgt * pf.z};
+    float4 va = S.nvp[t], vb = S.nvp[u];
+    float a[3] = {va.x - cx, va.y - cy, va.z - cz};
+    float b[3] = {vb.x - cx, vb.y - cy, vb.z - cz};
+    float det = g[0] * (a[1] * b[2] - a[2] * b[1]) + g[1] * (a[2] * b[0] - a[0] * b[2]) +
+                g[2] * (a[0] * b[1] - a[1] * b[0]);
+    V += det;
+    Mx += det * (g[0] + a[0] + b[0]);
+    My += det * (g[1] + a[1] + b[1]);
+    Mz += det * (g[2] + a[2] + b[2]);
+    if (S.pid[fy] < 0) continue;  // box faces do not move
+    float e1[3] = {a[0] - g[0], a[1] - g[1], a[2] - g[2]};
+    float e2[3] = {b[0] - g[0], b[1] - g[1], b[2] - g[2]};
+    float cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2], cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+    float al = 0.5f * (cr0 * pf.x + cr1 * pf.y + cr2 * pf.z);
+    float s[3] = {g[0] + a[0] + b[0], g[1] + a[1] + b[1], g[2] + a[2] + b[2]};
+    float* A = SM.acc[fy];
+    atomicAdd(&A[0], al);
+#pragma unroll
+    for (int k = 0; k < 3; k++) atomicAdd(&A[1 + k], al * s[k] * (1.0f / 3.0f));
+    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      int p = ii[k], r = jj[k];
+      float m2 = g[p] * g[r] + a[p] * a[r] + b[p] * b[r] + s[p] * s[r];
+      atomicAdd(&A[4 + k], al * m2 * (1.0f / 12.0f));
+    }
+  }
+  V = warp_sumf(V) * (1.0f / 6.0f);
+  Mx = warp_sumf(Mx) * (1.0f / 24.0f);
+  My = warp_sumf(My) * (1.0f / 24.0f);
+  Mz = warp_sumf(Mz) * (1.0f / 24.0f);
+  __syncwarp();
+  if (!(V > 0.f)) return true;
+  // local centroid g~ (relative to p_i) and the loss coefficients
+  const float gx = cx + Mx / V, gy = cy + My / V, gz = cz + Mz / V;
+  float gv = B.gvol ? B.gvol[orig_i] : 0.f;
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+  if (B.gcen) {
+    d0 = B.gcen[3 * (size_t)orig_i];
+    d1 = B.gcen[3 * (size_t)orig_i + 1];
+    d2 = B.gcen[3 * (size_t)orig_i + 2];
+  }
+  const float b0 = d0 / V, b1 = d1 / V, b2 = d2 / V;
+  const float ap = gv - (b0 * gx + b1 * gy + b2 * gz);
+  float gpi0 = 0.f, gpi1 = 0.f, gpi2 = 0.f, gwi = 0.f;
+#pragma unroll
+  for (int w = 0; w < NPW; w++) {
+    int f = 32 * w + (int)lane;
+    if (!((alive[w] >> lane) & 1u) || S.pid[f] < 0) continue;
+    const float* A = SM.acc[f];
+    float Ar = A[0];
+    float iy[3] = {A[1], A[2], A[3]};
+    float Syy[3][3] = {{A[4], A[7], A[8]}, {A[7], A[5], A[9]}, {A[8], A[9], A[6]}};
+    float cc[3] = {cx, cy, cz};
+    // shift the moments from the vertex mean c to the site p_i
+    float Am[3], St[3][3];
+#pragma unroll
+    for (int p = 0; p < 3; p++) Am[p] = Ar * cc[p] + iy[p];
+#pragma unroll
+    for (int p = 0; p < 3; p++)
+#pragma unroll
+      for (int r = 0; r < 3; r++) St[p][r] = Ar * cc[p] * cc[r] + cc[p] * iy[r] + iy[p] * cc[r] + Syy[p][r];
+    int js = S.pid[f];
+    float4 qj = P.sites[js];
+    float n[3] = {qj.x - c.me.x, qj.y - c.me.y, qj.z - c.me.z};
+    float D = sqrtf(fmaf(n[0], n[0], fmaf(n[1], n[1], n[2] * n[2])));
+    float iD = 1.0f / D;
+    float bb[3] = {b0, b1, b2};
+    float amb = Am[0] * b0 + Am[1] * b1 + Am[2] * b2;
+    float Sb[3];
+#pragma unroll
+    for (int p = 0; p < 3; p++) Sb[p] = St[p][0] * b0 + St[p][1] * b1 + St[p][2] * b2;
+    int oj = P.perm[js];
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+      float gj = (ap * (Ar * n[p] - Am[p]) + n[p] * amb - Sb[p]) * iD;
+      atomicAdd(&B.gp[3 * (size_t)oj + p], gj);
+    }
+    gpi0 += (ap * Am[0] + Sb[0]) * iD;
+    gpi1 += (ap * Am[1] + Sb[1]) * iD;
+    gpi2 += (ap * Am[2] + Sb[2]) * iD;
+    float gwc = (ap * Ar + amb) * 0.5f * iD;
+    gwi += gwc;
+    if (B.gw) atomicAdd(&B.gw[oj], -gwc);
+    (void)bb;
+  }
+  gpi0 = warp_sumf(gpi0);
+  gpi1 = warp_sumf(gpi1);
+  gpi2 = warp_sumf(gpi2);
+  gwi = warp_sumf(gwi);
+  if (lane == 0) {
+    atomicAdd(&B.gp[3 * (size_t)orig_i], gpi0);
+    atomicAdd(&B.gp[3 * (size_t)orig_i + 1], gpi1);
+    atomicAdd(&B.gp[3 * (size_t)orig_i + 2], gpi2);
+    if (B.gw) atomicAdd(&B.gw[orig_i], gwi);
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int VPL, int PCAP, int QPL, bool BIG>
+__global__ void back_kernel(BackBuffers B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BackSmem<VPL, PCAP>* Sw = reinterpret_cast<BackSmem<VPL, PCAP>*>(smem_raw);
+  BackSmem<VPL, PCAP>& S = Sw[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  Counters ct = {0, 0, 0, 0, 0, 0, 0};
+  const int total = BIG ? min(*B.list_count, B.list_cap) : B.c.n;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&B.work[BIG ? 1 : 0], 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= total) break;
+    int si = BIG ? B.list[item] : item;
+    bool ok = back_cell<VPL, PCAP, QPL>(B, S, si, ct);
+    if (!ok && lane == 0) {
+      if (BIG) {
+        set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
+      } else {
+        int k = atomicAdd(B.list_count, 1);
+        if (k < B.list_cap)
+          B.list[k] = si;
+        else
+          set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
+      }
+    }
+  }
+  long long f64 = ct.fp64, f64a = ct.fp64amb;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    f64 += __shfl_xor_sync(FULL, f64, o);
+    f64a += __shfl_xor_sync(FULL, f64a, o);
+  }
+  if (lane == 0) {
+    if (f64) atomicAdd((unsigned long long*)&B.c.st->fp64_fallbacks, (unsigned long long)f64);
+    if (f64a) atomicAdd((unsigned long long*)&B.c.st->fp64_ambiguous, (unsigned long long)f64a);
+  }
+}
+
+template <int VPL, int PCAP, int QPL, bool BIG>
+static cudaError_t launch_back_variant(const BackBuffers& b, int num_sms, int wpb, int grid_override,
+                                       cudaStream_t s) {
+  size_t smem = sizeof(BackSmem<VPL, PCAP>) * (size_t)wpb;
+  auto kern = back_kernel<VPL, PCAP, QPL, BIG>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * wpb, smem);
+  if (err != cudaSuccess) return err;
+  int grid = grid_override > 0 ? grid_override : num_sms * (occ > 0 ? occ : 1);
+  kern<<<grid, 32 * wpb, smem, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s) {
+  cudaError_t err = launch_back_variant<4, 64, 1, false>(b, num_sms, 4, 0, s);
+  if (err != cudaSuccess) return err;
+  return launch_back_variant<8, 192, 1, true>(b, num_sms, 4, num_sms * 2, s);
+}
+
+__global__ void inverse_perm_kernel(const int* __restrict__ perm, int n, int* __restrict__ inv) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) inv[perm[k]] = k;
+}
+
+cudaError_t launch_inverse_perm(const int* perm, int n, int* inv, cudaStream_t s) {
+  int blocks = min((n + 255) / 256, 4096);
+  inverse_perm_kernel<<<blocks, 256, 0, s>>>(perm, n, inv);
+  return cudaGetLastError();
+}
+
+}  // namespace vd

@@ -1,0 +1,256 @@
+// vd_internal.cuh -- device-side types and helpers shared by libvd's kernels.
+//
+// Coordinates inside a cell are local to its site (x~ = x - p_i). A plane is
+// stored normalised: unit outward normal n^, offset b^ = signed distance of
+// the plane from p_i (the d_ij of Eq. 2 for site planes), and e = an upper
+// bound on |b^ - b^_exact| plus the rounding of one sign test against it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <functional>
+
+#include "vd.h"
+
+namespace vd {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxLeaf = 32;            // leaf sizes 1..32 (one site per lane)
+constexpr int kMaxSites = 1 << 26;      // leaf refs pack the first site in 26 bits
+constexpr int kMaxSets = 1024;
+constexpr uint32_t kEmptyTri = 0xffffffffu;
+
+// Leaf references: bit 31 set, bits 26..30 = count-1, bits 0..25 = first.
+__host__ __device__ inline int make_leaf_ref(int first, int count) {
+  return (int)(0x80000000u | ((uint32_t)(count - 1) << 26) | (uint32_t)first);
+}
+__host__ __device__ inline bool ref_is_leaf(int ref) { return ref < 0; }
+__host__ __device__ inline int leaf_first(int ref) { return (int)((uint32_t)ref & 0x03ffffffu); }
+__host__ __device__ inline int leaf_count(int ref) { return (int)(((uint32_t)ref >> 26) & 31u) + 1; }
+
+// ---------------------------------------------------------------- status
+struct DevStatus {
+  int error;
+  int ovf_count;   // cells queued for the large-capacity pass
+  long long nnz;
+  long long empty_cells;
+  long long overflow_cells;
+  long long failed_cells;
+  long long fp64_fallbacks;
+  long long fp64_ambiguous;
+  long long candidates;
+  long long clips;
+  long long nodes;
+  long long vertex_tests;
+  long long new_vertices;
+};
+
+__device__ inline void set_error(DevStatus* st, int code) { atomicCAS(&st->error, 0, code); }
+
+// Per-set data of a (batched) build. Single builds use one set.
+struct SetInfo {
+  float lo[3], hi[3];
+  int first;      // first site (original and sorted index space coincide per set)
+  int count;
+  int root;       // root reference (internal node index or leaf ref)
+  int weighted;
+};
+
+// ---------------------------------------------------------------- numerics
+template <typename T>
+struct Num;
+template <>
+struct Num<float> {
+  static constexpr float u = 5.9604644775390625e-8f;  // 2^-24
+};
+template <>
+struct Num<double> {
+  static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+};
+
+template <typename T>
+struct PlaneT {
+  T nx, ny, nz, b, e;
+};
+
+// Radical plane of site q (weight wj) in the frame of site p (weight wi):
+// n.x~ <= (|n|^2 + wi - wj)/2 with n = q - p (Eq. 1), normalised so that b
+// is the power distance d_ij of Eq. 2. Error bound derivation: n_k carries
+// one rounding, |n|^2 at most 5.1u relative, b = (|n|^2 + (wi-wj))/2 at most
+// 3.1u (|n|^2+|wi|+|wj|), 1/|n| at most 4.6u and each product one more u;
+// 9u|b| also covers the rounding of one fused sign test.
+template <typename T>
+__device__ __forceinline__ PlaneT<T> site_plane(T px, T py, T pz, T wi, T qx, T qy, T qz, T wj) {
+  const T u = Num<T>::u;
+  T nx = qx - px, ny = qy - py, nz = qz - pz;
+  T nn = fma(nx, nx, fma(ny, ny, nz * nz));
+  T r = T(1) / sqrt(nn);
+  T b = T(0.5) * (nn + (wi - wj));
+  PlaneT<T> P;
+  P.nx = nx * r;
+  P.ny = ny * r;
+  P.nz = nz * r;
+  P.b = b * r;
+  P.e = T(4) * u * (nn + fabs(wi) + fabs(wj)) * r + T(9) * u * fabs(P.b);
+  return P;
+}
+
+// Box face f (0:+x 1:-x 2:+y 3:-y 4:+z 5:-z) in the frame of p.
+template <typename T>
+__device__ __forceinline__ PlaneT<T> box_plane(int f, T px, T py, T pz, const float* lo, const float* hi) {
+  const T u = Num<T>::u;
+  int ax = f >> 1;
+  T pc = ax == 0 ? px : (ax == 1 ? py : pz);
+  PlaneT<T> P;
+  P.nx = P.ny = P.nz = T(0);
+  T s = (f & 1) ? T(-1) : T(1);
+  if (ax == 0) P.nx = s;
+  if (ax == 1) P.ny = s;
+  if (ax == 2) P.nz = s;
+  P.b = (f & 1) ? (pc - T(lo[ax])) : (T(hi[ax]) - pc);
+  P.e = T(5) * u * fabs(P.b);
+  return P;
+}
+
+// Vertex of planes (A, B, C) with det(nA, nB, nC) > 0 (orientation
+// invariant), by Cramer's rule, and a bound e on |x - x_exact|_2 plus the
+// rounding of a later sign test n^.x - b (first-order perturbation of the
+// 3x3 system: |N^-1| <= sqrt(3)/W for unit normals, normal entries off by
+// at most 8u, offsets by A.e etc.). e = inf when W is too small for the
+// first-order bound to hold.
+template <typename T>
+__device__ __forceinline__ void vertex3(const PlaneT<T>& A, const PlaneT<T>& B, const PlaneT<T>& C, T& x, T& y,
+                                        T& z, T& e) {
+  const T u = Num<T>::u;
+  const T epsn = T(8) * u;
+  T c1x = fma(B.ny, C.nz, -B.nz * C.ny), c1y = fma(B.nz, C.nx, -B.nx * C.nz), c1z = fma(B.nx, C.ny, -B.ny * C.nx);
+  T c2x = fma(C.ny, A.nz, -C.nz * A.ny), c2y = fma(C.nz, A.nx, -C.nx * A.nz), c2z = fma(C.nx, A.ny, -C.ny * A.nx);
+  T c3x = fma(A.ny, B.nz, -A.nz * B.ny), c3y = fma(A.nz, B.nx, -A.nx * B.nz), c3z = fma(A.nx, B.ny, -A.ny * B.nx);
+  T W = fma(A.nx, c1x, fma(A.ny, c1y, A.nz * c1z));
+  T iw = T(1) / W;
+  x = fma(A.b, c1x, fma(B.b, c2x, C.b * c3x)) * iw;
+  y = fma(A.b, c1y, fma(B.b, c2y, C.b * c3y)) * iw;
+  z = fma(A.b, c1z, fma(B.b, c2z, C.b * c3z)) * iw;
+  T x1 = fabs(x) + fabs(y) + fabs(z);
+  if (!(W > T(1024) * u) || !(x1 < T(1e30))) {
+    e = T(INFINITY);
+  } else {
+    T ep = (T(1.75) * (A.e + B.e + C.e) + (T(5.25) * epsn + T(9) * u) * x1 +
+            T(6) * u * (fabs(A.b) + fabs(B.b) + fabs(C.b))) * iw + u * x1;
+    e = T(1.1) * ep + (epsn + T(3) * u) * x1;
+  }
+}
+
+// Sign test value s = n^.x - b (>0: outside) and whether it is certain.
+template <typename T>
+__device__ __forceinline__ T side(const PlaneT<T>& H, T x, T y, T z) {
+  return fma(H.nx, x, fma(H.ny, y, fma(H.nz, z, -H.b)));
+}
+
+template <typename T>
+__device__ __forceinline__ bool ambiguous(T s, T ev, T eh) {
+  return fabs(s) <= (ev + eh) * (T(1) + T(4) * Num<T>::u);
+}
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+// monotone map float -> uint32 (for redux.sync min/max)
+__device__ __forceinline__ uint32_t f2o(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t o) {
+  uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ float warp_minf(float v) { return o2f(__reduce_min_sync(FULL, f2o(v))); }
+__device__ __forceinline__ float warp_maxf(float v) { return o2f(__reduce_max_sync(FULL, f2o(v))); }
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- host-side launchers
+struct BvhBuffers {
+  // sorting
+  uint64_t* keys;
+  uint64_t* keys_alt;
+  int* vals;
+  int* vals_alt;
+  unsigned* hist;      // [256 * 2 * kSortBlocksMax]
+  // Karras tree
+  int* left;
+  int* right;
+  int* parent;         // [2n-1]: parents of internal nodes then of sites
+  int2* range;
+  int* visit;
+  float4* box_lo;      // per internal node: lo.xyz, maxw
+  float4* box_hi;      // hi.xyz
+  float4* nodes;       // [n-1][4] traversal records
+};
+
+struct CellBuffers {
+  const float4* sites;   // sorted packed sites
+  const int* perm;       // sorted -> original index
+  const float4* nodes;
+  const uint64_t* keys;  // sorted keys (set id in the top bits)
+  const SetInfo* sets;
+  int nsets;
+  int set_shift;
+  int n;
+  int* counts;           // [n] by original index
+  int* scratch;          // [n * stride]
+  int stride;
+  int* scratch_big;      // [ovf_cap * stride_big]
+  int stride_big;
+  int* ovf_list;         // [ovf_cap] sorted indices of overflowed cells
+  int ovf_cap;
+  int* ovf_slot;         // [n] by original index: row in scratch_big or -1
+  float* vol;
+  float* cen;
+  int* work;             // [2] work counters (main pass, overflow pass)
+  DevStatus* st;
+  vd_config cfg;
+};
+
+constexpr int kSortThreads = 512;
+constexpr int kSortBlocksMax = 1024;
+
+struct BackBuffers {
+  CellBuffers c;
+  const int* inv_perm;  // original -> sorted index
+  const float* gvol;
+  const float* gcen;
+  float* gp;
+  float* gw;
+  int* list;            // cells that overflowed the small variant
+  int* list_count;
+  int list_cap;
+  int* work;            // [2]
+};
+
+cudaError_t launch_pack_keys(const float* xyz, const float* w, int n, const SetInfo* sets, int nsets,
+                             const int* unused, int set_shift, uint64_t* keys, int* vals, DevStatus* st,
+                             cudaStream_t s);
+cudaError_t radix_sort_pairs(uint64_t*& keys, uint64_t*& keys_alt, int*& vals, int*& vals_alt, unsigned* hist,
+                             int n, int bits, cudaStream_t s);
+cudaError_t launch_gather_sites(const float* xyz, const float* w, const int* perm, int n, const SetInfo* sets,
+                                const uint64_t* keys, int set_shift, int nsets, float4* sites, cudaStream_t s);
+cudaError_t launch_build_bvh(const uint64_t* keys, const float4* sites, int n, int leaf_size, BvhBuffers& b,
+                             SetInfo* sets, int nsets, DevStatus* st, cudaStream_t s);
+cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, const std::function<void()>& between);
+cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbors, int64_t cap, int64_t* nnz_out,
+                       long long* block_sums, int32_t* user_status, bool recount, cudaStream_t s);
+cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s);
+cudaError_t launch_inverse_perm(const int* perm, int n, int* inv, cudaStream_t s);
+
+}  // namespace vd
