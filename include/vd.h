@@ -81,7 +81,7 @@ typedef struct {
 typedef struct {
   int32_t leaf_size;       /* LBVH leaf size (1..32); default 16                     */
   int32_t verts_per_lane;  /* polytope capacity per cell = 32 * this (2 or 4)        */
-  int32_t queue_per_lane;  /* best-first queue capacity per cell = 32 * this (1, 2)  */
+  int32_t queue_per_lane;  /* best-first queue capacity per cell = 32 * this (1,2,4,8)*/
   int32_t cull_mode;       /* 0 directional (Sec. 4.2.1), 1 isotropic (single       */
                            /*   radius, ablation), 2 none (every site is clipped)   */
   int32_t traversal;       /* 0 best-first (Alg. 1), 1 depth-first (ablation)        */
@@ -106,6 +106,10 @@ typedef struct {
   int64_t nodes;              /* counters=1: BVH nodes tested                       */
   int64_t vertex_tests;       /* counters=1: vertex-plane sign tests                */
   int64_t new_vertices;       /* counters=1: vertices created                       */
+  int64_t refined_vertices;   /* ill-conditioned vertices recomputed in FP64         */
+  int64_t refined_volumes;    /* cells whose volume/centroid were integrated in FP64 */
+  int64_t overflow_reason[4]; /* register-path overflows by cause: queue, vertices,  */
+                              /*   planes, neighbours (> 64 per row)                */
 } vd_status;
 
 /* Per-phase device times of the last call, from CUDA events recorded on the

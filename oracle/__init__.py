@@ -56,7 +56,7 @@ def _load():
             I64 = ctypes.c_int64
             I32 = ctypes.c_int32
             C = ctypes.c_int
-            lib.oracle_cells.argtypes = [P, P, I64, P, P, P, I64, C, C, P, P, I32, P, P, P, P, P, C]
+            lib.oracle_cells.argtypes = [P, P, I64, P, P, P, I64, C, C, P, P, P, I64, P, P, P, P, P, C]
             lib.oracle_cells.restype = C
             lib.oracle_grad.argtypes = [P, P, I64, P, P, P, I64, P, P, P, P, P, C]
             lib.oracle_grad.restype = C
@@ -93,42 +93,49 @@ def _threads(threads):
 
 
 def cells(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, mode="kd", exact=False,
-          threads=None, max_nbrs=512):
+          threads=None, max_nbrs=None):
     """Cells of the listed sites (all if ``cells`` is None).
 
     Returns a dict: ``counts`` int32[m], ``nbrs`` list of ascending int32
     arrays, ``offsets``/``indices`` (CSR), ``vol`` float64[m], ``cen``
     float64[m,3], ``nverts``/``nfaces`` int32[m] and ``stats`` (dict).
     """
+    del max_nbrs  # neighbour lists are unbounded (kept for call compatibility)
     lib = _load()
     xyz, w, lo, hi = _prep(xyz, w, bbox)
     n = xyz.shape[0]
     idx = None if cells is None else np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
     m = n if idx is None else idx.shape[0]
-    counts = np.zeros(m, np.int32)
-    nbrs = np.full((m, max_nbrs), -1, np.int32)
-    vol = np.zeros(m, np.float64)
-    cen = np.zeros((m, 3), np.float64)
-    nv = np.zeros(m, np.int32)
-    nf = np.zeros(m, np.int32)
-    st = np.zeros(lib.oracle_stat_count(), np.int64)
-    rc = lib.oracle_cells(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(idx), m,
-                          0 if mode == "brute" else 1, 1 if exact else 0, _ptr(counts), _ptr(nbrs),
-                          max_nbrs, _ptr(vol), _ptr(cen), _ptr(nv), _ptr(nf), _ptr(st), _threads(threads))
-    _check(rc)
-    offsets = np.zeros(m + 1, np.int64)
-    np.cumsum(counts, out=offsets[1:])
-    indices = np.concatenate([nbrs[q, : counts[q]] for q in range(m)]) if m else np.zeros(0, np.int32)
+    cap = 20 * m + 1024
+    while True:
+        counts = np.zeros(m, np.int32)
+        offsets = np.zeros(m + 1, np.int64)
+        nb = np.zeros(cap, np.int32)
+        vol = np.zeros(m, np.float64)
+        cen = np.zeros((m, 3), np.float64)
+        nv = np.zeros(m, np.int32)
+        nf = np.zeros(m, np.int32)
+        st = np.zeros(lib.oracle_stat_count() + 1, np.int64)
+        rc = lib.oracle_cells(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(idx), m,
+                              0 if mode == "brute" else 1, 1 if exact else 0, _ptr(counts), _ptr(offsets),
+                              _ptr(nb), cap, _ptr(vol), _ptr(cen), _ptr(nv), _ptr(nf), _ptr(st),
+                              _threads(threads))
+        if rc == -3 and st[-1] > cap:
+            cap = int(st[-1])
+            continue
+        _check(rc)
+        break
+    indices = nb[: offsets[-1]].copy()
     return {
         "counts": counts,
         "offsets": offsets,
-        "indices": indices.astype(np.int32),
-        "nbrs": [nbrs[q, : counts[q]].copy() for q in range(m)],
+        "indices": indices,
+        "nbrs": np.split(indices, offsets[1:-1]) if m else [],
         "vol": vol,
         "cen": cen,
         "nverts": nv,
         "nfaces": nf,
-        "stats": dict(zip(STAT_NAMES, st.tolist())),
+        "stats": dict(zip(STAT_NAMES, st[:-1].tolist())),
     }
 
 

@@ -129,6 +129,10 @@ typedef struct {
   int64_t* X;  /* [3n] coordinate * 2^20 */
   int64_t* W;  /* [n]  weight * 2^40     */
   int64_t LO[3], HI[3];
+  /* sites with an exact duplicate that beats them (larger weight, then lower
+   * index): their cells are empty and their half-spaces are implied by the
+   * winner's, so they are never candidates */
+  unsigned char* dup_loser;
 } problem_t;
 
 static double dmax(double a, double b) { return a > b ? a : b; }
@@ -603,22 +607,33 @@ static void kd_free(kdtree_t* T) {
   free(T->idx);
 }
 
-/* lower bound of d_ij over all sites of a node (Sec. 4.2.2) */
+/* Lower bound of d_ij over all sites of a node (Sec. 4.2.2). A site j of
+ * the node lies at distance D in [dmin, dmax] from p_i (nearest and
+ * farthest point of the node's box) and has w_j <= wmax, so
+ *   d_ij = D/2 + (w_i - w_j)/(2D) >= f(D) = D/2 + c/(2D),  c = w_i - wmax.
+ * For c <= 0, f increases with D and the bound is f(dmin) (the paper's);
+ * for c > 0, f is convex with its minimum at D = sqrt(c), so the bound is
+ * f at sqrt(c) clamped to [dmin, dmax]. */
 static double node_lower_bound(const problem_t* pr, int64_t i, const kdnode_t* nd) {
-  double d2 = 0.0;
+  double d2 = 0.0, f2 = 0.0;
   for (int k = 0; k < 3; k++) {
     double c = pr->xyz[3 * i + k];
     double e = 0.0;
     if (c < nd->lo[k]) e = nd->lo[k] - c;
     if (c > nd->hi[k]) e = c - nd->hi[k];
     d2 += e * e;
+    double f = dmax(fabs(c - nd->lo[k]), fabs(nd->hi[k] - c));
+    f2 += f * f;
   }
-  if (d2 == 0.0) return -INFINITY;
-  double d = sqrt(d2);
   double wi = pr->w ? pr->w[i] : 0.0;
   double c = wi - nd->wmax;
-  if (c >= 0.0) return 0.5 * d;
-  return 0.5 * d + c / (2.0 * d);
+  double D = sqrt(d2);
+  if (c > 0.0) {
+    double s = sqrt(c), dm = sqrt(f2);
+    D = s < D ? D : (s > dm ? dm : s);
+  }
+  if (D == 0.0) return -INFINITY;
+  return 0.5 * D + c / (2.0 * D);
 }
 
 /* binary min-heap of (key, kind, id) */
@@ -709,6 +724,7 @@ static void sort_candidates(int64_t* idx, double* key, int64_t n, int64_t* tmpi,
 /* process candidate j for cell i; returns <0 on error, 1 if the cell
  * became empty */
 static int offer_candidate(const problem_t* pr, int64_t i, int64_t j, cell_t* C, int64_t* stats) {
+  if (pr->dup_loser[j]) return 0; /* implied by its duplicate's plane */
   if (is_duplicate(pr, i, j)) {
     if (duplicate_beats(pr, i, j)) {
       C->empty = 1;
@@ -727,6 +743,12 @@ static int offer_candidate(const problem_t* pr, int64_t i, int64_t j, cell_t* C,
 static int build_cell(const problem_t* pr, const kdtree_t* T, int mode, int64_t i, cell_t* C,
                       qscratch_t* S, int64_t* stats) {
   cell_start(pr, i, C);
+  if (pr->dup_loser[i]) { /* an exact duplicate site beats this one */
+    C->empty = 1;
+    C->nv = 0;
+    stats[ST_EMPTY]++;
+    return 0;
+  }
   if (mode == 0) {
     /* brute force: every other site, ascending d_ij */
     int64_t m = 0;
@@ -867,6 +889,45 @@ static int cell_volume(const cell_t* C, double* vol, double mom[3], int* poly, i
 /* ------------------------------------------------------------------ */
 /* public entry points                                                  */
 
+static const problem_t* g_cmp_pr;
+
+static int cmp_position(const void* A, const void* B) {
+  int64_t a = *(const int64_t*)A, b = *(const int64_t*)B;
+  const float* x = g_cmp_pr->xyz;
+  for (int k = 0; k < 3; k++) {
+    if (x[3 * a + k] < x[3 * b + k]) return -1;
+    if (x[3 * a + k] > x[3 * b + k]) return 1;
+  }
+  return a < b ? -1 : (a > b);
+}
+
+static void mark_duplicate_losers(problem_t* pr) {
+  int64_t n = pr->n;
+  pr->dup_loser = (unsigned char*)xrealloc(NULL, (size_t)n);
+  memset(pr->dup_loser, 0, (size_t)n);
+  int64_t* idx = (int64_t*)xrealloc(NULL, sizeof(int64_t) * (size_t)n);
+  for (int64_t q = 0; q < n; q++) idx[q] = q;
+  g_cmp_pr = pr;
+  qsort(idx, (size_t)n, sizeof(int64_t), cmp_position);
+  for (int64_t a = 0; a < n;) {
+    int64_t b = a + 1;
+    while (b < n && pr->xyz[3 * idx[b]] == pr->xyz[3 * idx[a]] && pr->xyz[3 * idx[b] + 1] == pr->xyz[3 * idx[a] + 1] &&
+           pr->xyz[3 * idx[b] + 2] == pr->xyz[3 * idx[a] + 2])
+      b++;
+    for (int64_t u = a; u < b; u++)
+      for (int64_t v = a; v < b; v++)
+        if (u != v && duplicate_beats(pr, idx[u], idx[v])) pr->dup_loser[idx[u]] = 1;
+    a = b;
+  }
+  free(idx);
+}
+
+static void free_problem(problem_t* pr) {
+  free(pr->X);
+  free(pr->W);
+  free(pr->dup_loser);
+}
+
 static int setup_problem(problem_t* pr, const float* xyz, const float* w, int64_t n, const float* lo,
                          const float* hi, int exact) {
   memset(pr, 0, sizeof(*pr));
@@ -906,29 +967,42 @@ static int setup_problem(problem_t* pr, const float* xyz, const float* w, int64_
       pr->HI[k] = (int64_t)b;
     }
   }
+  mark_duplicate_losers(pr);
   return 0;
 }
 
-static void free_problem(problem_t* pr) {
-  free(pr->X);
-  free(pr->W);
-}
+
 
 /*
  * oracle_cells: neighbours, volume and centroid of the requested cells.
  *   xyz [3n] float32 sites, w [n] float32 weights or NULL, lo/hi [3] box.
  *   cells [ncells] int64 site indices (NULL: all n, in order).
  *   mode 0 = brute force, 1 = k-d tree. exact 1 = integer predicates.
- *   counts [ncells] int32, nbrs [ncells*max_nbrs] int32 (ascending),
+ *   counts [ncells] int32, offsets [ncells+1] int64 and nbrs [nbr_cap] int32
+ *   (CSR, ascending within a row; if the total exceeds nbr_cap nothing is
+ *   written to nbrs and stats[ST_N] receives the required size),
  *   vol [ncells], cen [3*ncells] float64, nverts / nfaces [ncells] int32
  *   (may be NULL), stats [ST_N] int64 (summed over cells).
- * Returns 0 or a negative error code.
+ * Returns 0 or a negative error code. stats has ST_N + 1 entries.
  */
+typedef struct {
+  int32_t* v;
+  int64_t n, cap;
+} ibuf_t;
+
+static void ibuf_push(ibuf_t* b, int32_t x) {
+  if (b->n == b->cap) {
+    b->cap = b->cap ? 2 * b->cap : 4096;
+    b->v = (int32_t*)xrealloc(b->v, sizeof(int32_t) * (size_t)b->cap);
+  }
+  b->v[b->n++] = x;
+}
+
 int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi,
                  const int64_t* cells, int64_t ncells, int mode, int exact, int32_t* counts,
-                 int32_t* nbrs, int32_t max_nbrs, double* vol, double* cen, int32_t* nverts,
+                 int64_t* offsets, int32_t* nbrs, int64_t nbr_cap, double* vol, double* cen, int32_t* nverts,
                  int32_t* nfaces, int64_t* stats, int nthreads) {
-  if (n <= 0 || !xyz || !lo || !hi || !counts || !vol || !cen || !stats) return ORC_ERR_ARG;
+  if (n <= 0 || !xyz || !lo || !hi || !counts || !offsets || !vol || !cen || !stats) return ORC_ERR_ARG;
   problem_t pr;
   int rc = setup_problem(&pr, xyz, w, n, lo, hi, exact);
   if (rc) {
@@ -939,15 +1013,27 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
   kdtree_t T;
   memset(&T, 0, sizeof(T));
   if (mode == 1) kd_build(&T, &pr);
-  for (int k = 0; k < ST_N; k++) stats[k] = 0;
+  for (int k = 0; k <= ST_N; k++) stats[k] = 0;
   int err = 0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
+  int nth = omp_get_max_threads();
 #else
   (void)nthreads;
+  int nth = 1;
 #endif
+  /* per-thread neighbour lists, copied out in cell order afterwards */
+  ibuf_t* tb = (ibuf_t*)calloc((size_t)nth, sizeof(ibuf_t));
+  int64_t* where = (int64_t*)xrealloc(NULL, sizeof(int64_t) * (size_t)(ncells > 0 ? ncells : 1));
+  int* owner = (int*)xrealloc(NULL, sizeof(int) * (size_t)(ncells > 0 ? ncells : 1));
 #pragma omp parallel
   {
+#ifdef _OPENMP
+    int tid = omp_get_thread_num();
+#else
+    int tid = 0;
+#endif
+    ibuf_t* mybuf = &tb[tid];
     cell_t C;
     cell_init_storage(&C);
     qscratch_t S;
@@ -958,7 +1044,9 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
     }
     int polycap = 4096;
     int* poly = (int*)xrealloc(NULL, sizeof(int) * polycap);
-    int* nb = (int*)xrealloc(NULL, sizeof(int) * 4096);
+    int nbcap = 4096;
+    int* nb = (int*)xrealloc(NULL, sizeof(int) * (size_t)nbcap);
+    int64_t* tmpn = (int64_t*)xrealloc(NULL, sizeof(int64_t) * (size_t)nbcap);
     int64_t st[ST_N];
     for (int k = 0; k < ST_N; k++) st[k] = 0;
 #pragma omp for schedule(dynamic, 8)
@@ -976,6 +1064,8 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
         continue;
       }
       double p[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+      where[q] = 0;
+      owner[q] = tid;
       if (C.empty || C.nv == 0) {
         counts[q] = 0;
         vol[q] = 0.0;
@@ -985,16 +1075,15 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
         continue;
       }
       /* neighbours: site planes referenced by a final vertex */
-      if (C.npl > 4096) {
-#pragma omp atomic write
-        err = ORC_ERR_NBR_CAP;
-        continue;
+      if (C.npl > nbcap) {
+        nbcap = 2 * C.npl;
+        nb = (int*)xrealloc(nb, sizeof(int) * (size_t)nbcap);
+        tmpn = (int64_t*)xrealloc(tmpn, sizeof(int64_t) * (size_t)nbcap);
       }
       for (int f = 0; f < C.npl; f++) nb[f] = 0;
       for (int k = 0; k < C.nv; k++)
         for (int a = 0; a < 3; a++) nb[C.v[k].p[a]] = 1;
       int cnt = 0, nf = 0;
-      int64_t tmpn[4096];
       for (int f = 0; f < C.npl; f++)
         if (nb[f]) {
           nf++;
@@ -1010,14 +1099,9 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
         }
         tmpn[b + 1] = x;
       }
-      if (cnt > max_nbrs) {
-#pragma omp atomic write
-        err = ORC_ERR_NBR_CAP;
-        continue;
-      }
       counts[q] = cnt;
-      if (nbrs)
-        for (int a = 0; a < cnt; a++) nbrs[(int64_t)q * max_nbrs + a] = (int32_t)tmpn[a];
+      where[q] = mybuf->n;
+      for (int a = 0; a < cnt; a++) ibuf_push(mybuf, (int32_t)tmpn[a]);
       if (nverts) nverts[q] = C.nv;
       if (nfaces) nfaces[q] = nf;
       double V, M[3];
@@ -1044,9 +1128,23 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
     free(S.heap.a);
     free(poly);
     free(nb);
+    free(tmpn);
   }
   if (mode == 1) kd_free(&T);
   free_problem(&pr);
+  offsets[0] = 0;
+  for (int64_t q = 0; q < ncells; q++) offsets[q + 1] = offsets[q] + (err ? 0 : counts[q]);
+  stats[ST_N] = offsets[ncells];
+  if (!err && nbrs && offsets[ncells] <= nbr_cap) {
+    for (int64_t q = 0; q < ncells; q++)
+      if (counts[q] > 0) memcpy(nbrs + offsets[q], tb[owner[q]].v + where[q], sizeof(int32_t) * (size_t)counts[q]);
+  } else if (!err && offsets[ncells] > nbr_cap) {
+    err = ORC_ERR_NBR_CAP;
+  }
+  for (int t = 0; t < nth; t++) free(tb[t].v);
+  free(tb);
+  free(where);
+  free(owner);
   return err;
 }
 

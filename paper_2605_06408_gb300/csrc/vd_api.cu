@@ -7,14 +7,13 @@
 #include <cstring>
 #include <new>
 
-#include "vd_internal.cuh"
+#include "vd_big.cuh"
 
 using namespace vd;
 
 namespace {
 
 constexpr int kStride = 64;      // neighbour row stride of the register-resident pass
-constexpr int kStrideBig = 192;  // ... of the large-capacity pass
 constexpr int kHistEntries = 256 * 2 * kSortBlocksMax;
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -31,7 +30,9 @@ struct Layout {
   }
 };
 
-int64_t ovf_capacity(int64_t n) { return n / 16 > 4096 ? n / 16 : 4096; }
+int64_t ovf_capacity(int64_t n) { return n > 4096 ? n : 4096; }
+int64_t pool_capacity(int64_t n) { return n > (1 << 22) ? n : (1 << 22); }
+int big_warps(int num_sms) { return num_sms * kBigWarpsPerBlock; }
 
 }  // namespace
 
@@ -60,12 +61,16 @@ struct vd_ctx {
   float4* nodes = nullptr;
   int* counts = nullptr;
   int* scratch = nullptr;
-  int* scratch_big = nullptr;
+  int* pool = nullptr;
+  char* arena = nullptr;
+  unsigned char* loser = nullptr;
+  long long pool_cap = 0;
   int* ovf_list = nullptr;
   int* ovf_slot = nullptr;
   int* blist = nullptr;
   long long* block_sums = nullptr;
-  int* work = nullptr;  // [4]
+  int* work = nullptr;  // [8] work counters
+  unsigned* wrange = nullptr;  // [2] orderable min / max weight
   DevStatus* st = nullptr;
   SetInfo* sets_dev = nullptr;
   SetInfo* sets_host = nullptr;  // pinned staging
@@ -104,7 +109,8 @@ static int cuda_fail(cudaError_t e) {
 static int check_config(const vd_config* c) {
   if (c->leaf_size < 1 || c->leaf_size > kMaxLeaf) return VD_ERR_INVALID_ARG;
   if (c->verts_per_lane != 2 && c->verts_per_lane != 4) return VD_ERR_INVALID_ARG;
-  if (c->queue_per_lane != 1 && c->queue_per_lane != 2) return VD_ERR_INVALID_ARG;
+  if (c->queue_per_lane != 1 && c->queue_per_lane != 2 && c->queue_per_lane != 4 && c->queue_per_lane != 8)
+    return VD_ERR_INVALID_ARG;
   if (c->cull_mode < 0 || c->cull_mode > 2) return VD_ERR_INVALID_ARG;
   if (c->traversal < 0 || c->traversal > 1) return VD_ERR_INVALID_ARG;
   if (c->warps_per_block < 1 || c->warps_per_block > 16) return VD_ERR_INVALID_ARG;
@@ -122,7 +128,7 @@ static int release(vd_ctx* ctx) {
   return VD_OK;
 }
 
-static Layout make_layout(int64_t n) {
+static Layout make_layout(int64_t n, int num_sms) {
   Layout L;
   int64_t ovf = ovf_capacity(n);
   int64_t nb = (n + 8191) / 8192 + 1;
@@ -143,14 +149,16 @@ static Layout make_layout(int64_t n) {
   L.add(sizeof(float4) * 4 * n);       // 14 nodes
   L.add(sizeof(int) * n);              // 15 counts
   L.add(sizeof(int) * (size_t)n * kStride);        // 16 scratch
-  L.add(sizeof(int) * (size_t)ovf * kStrideBig);   // 17 scratch_big
+  L.add(sizeof(int) * (size_t)pool_capacity(n));   // 17 pool
   L.add(sizeof(int) * ovf);            // 18 ovf_list
   L.add(sizeof(int) * n);              // 19 ovf_slot
   L.add(sizeof(int) * ovf);            // 20 blist
   L.add(sizeof(long long) * nb);       // 21 block_sums
-  L.add(sizeof(int) * 8);              // 22 work
+  L.add(sizeof(int) * 16);             // 22 work (+ weight range)
   L.add(sizeof(DevStatus));            // 23 status
   L.add(sizeof(SetInfo) * kMaxSets);   // 24 sets
+  L.add(big_arena_bytes() * (size_t)big_warps(num_sms));  // 25 arenas
+  L.add((size_t)n);                    // 26 duplicate losers
   return L;
 }
 
@@ -160,7 +168,7 @@ static int reserve(vd_ctx* ctx, int64_t n) {
   if (ctx->cap_n > 0 && want < ctx->cap_n + ctx->cap_n / 4) want = ctx->cap_n + ctx->cap_n / 4;
   if (want > kMaxSites) want = kMaxSites;
   if (want < 1024) want = 1024;
-  Layout L = make_layout(want);
+  Layout L = make_layout(want, ctx->num_sms);
   release(ctx);
   cudaError_t e = cudaMalloc(&ctx->base, L.total);
   if (e != cudaSuccess) {
@@ -188,12 +196,16 @@ static int reserve(vd_ctx* ctx, int64_t n) {
   ctx->nodes = (float4*)(b + L.off[14]);
   ctx->counts = (int*)(b + L.off[15]);
   ctx->scratch = (int*)(b + L.off[16]);
-  ctx->scratch_big = (int*)(b + L.off[17]);
+  ctx->pool = (int*)(b + L.off[17]);
+  ctx->pool_cap = pool_capacity(want);
+  ctx->arena = b + L.off[25];
+  ctx->loser = (unsigned char*)(b + L.off[26]);
   ctx->ovf_list = (int*)(b + L.off[18]);
   ctx->ovf_slot = (int*)(b + L.off[19]);
   ctx->blist = (int*)(b + L.off[20]);
   ctx->block_sums = (long long*)(b + L.off[21]);
   ctx->work = (int*)(b + L.off[22]);
+  ctx->wrange = (unsigned*)(ctx->work + 8);
   ctx->st = (DevStatus*)(b + L.off[23]);
   ctx->sets_dev = (SetInfo*)(b + L.off[24]);
   return VD_OK;
@@ -203,6 +215,7 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   CellBuffers c;
   std::memset(&c, 0, sizeof(c));
   c.sites = ctx->sites;
+  c.loser = ctx->loser;
   c.perm = ctx->perm;
   c.nodes = ctx->nodes;
   c.keys = ctx->keys_sorted;
@@ -213,8 +226,9 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   c.counts = ctx->counts;
   c.scratch = ctx->scratch;
   c.stride = kStride;
-  c.scratch_big = ctx->scratch_big;
-  c.stride_big = kStrideBig;
+  c.pool = ctx->pool;
+  c.pool_cap = ctx->pool_cap;
+  c.arena = ctx->arena;
   c.ovf_list = ctx->ovf_list;
   c.ovf_cap = ctx->ovf_cap;
   c.ovf_slot = ctx->ovf_slot;
@@ -255,8 +269,12 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   cudaMemsetAsync(ctx->work, 0, sizeof(int) * 8, s);
   cudaMemsetAsync(ctx->ovf_slot, 0xff, sizeof(int) * (size_t)n, s);
   cudaMemsetAsync(ctx->counts, 0, sizeof(int) * (size_t)n, s);
-  // 1. Morton keys (per-set quantisation) and input validation
-  e = launch_pack_keys(xyz, w, n, ctx->sets_dev, nsets, nullptr, set_shift, ctx->keys_a, ctx->vals_a, ctx->st, s);
+  // 1. keys: (set, weight stratum, Morton code in the set's box); input validation
+  e = launch_weight_range(w, n, ctx->sets_dev, nsets, ctx->wrange, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  const int bin_shift = nsets > 1 ? 51 : 60;
+  e = launch_pack_keys(xyz, w, n, ctx->sets_dev, nsets, set_shift, bin_shift, ctx->wrange, ctx->keys_a,
+                       ctx->vals_a, ctx->st, s);
   if (e != cudaSuccess) return VD_ERR_CUDA;
   mark(ctx, 1, s);
   // 2. radix sort of (key, index)
@@ -274,6 +292,8 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   e = launch_gather_sites(xyz, w, ctx->perm, n, ctx->sets_dev, ctx->keys_sorted, set_shift, nsets, ctx->sites, s);
   if (e != cudaSuccess) return VD_ERR_CUDA;
   e = launch_inverse_perm(ctx->perm, n, ctx->inv_perm, s);
+  if (e != cudaSuccess) return VD_ERR_CUDA;
+  e = launch_mark_losers(ctx->keys_sorted, ctx->sites, ctx->perm, n, ctx->loser, s);
   if (e != cudaSuccess) return VD_ERR_CUDA;
   // 4. LBVH with per-node max weight (App. A.2)
   BvhBuffers b;
@@ -313,7 +333,8 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   ctx->ev_valid = ctx->cfg.timing != 0;
   ctx->ev_backward = false;
   int passes = (bits + 7) / 8;
-  ctx->launches = 1 + 3 * passes + 2 + (n >= 2 ? 4 : 1) + 2 + 3 + (out->neighbors && out->nnz_capacity > 0) + 1;
+  ctx->launches = (w ? 1 : 0) + 1 + 3 * passes + 3 + (n >= 2 ? 4 : 1) + 2 + 3 +
+                  (out->neighbors && out->nnz_capacity > 0) + 1;
   return VD_OK;
 }
 
@@ -323,7 +344,7 @@ int vd_default_config(vd_config* cfg) {
   if (!cfg) return VD_ERR_INVALID_ARG;
   cfg->leaf_size = 16;
   cfg->verts_per_lane = 2;
-  cfg->queue_per_lane = 2;
+  cfg->queue_per_lane = 4;
   cfg->cull_mode = 0;
   cfg->traversal = 0;
   cfg->warps_per_block = 4;
@@ -391,7 +412,14 @@ int vd_reserve(vd_ctx* ctx, int64_t n, int /*weighted*/) {
 size_t vd_workspace_bytes(int64_t n, int /*weighted*/) {
   if (n <= 0) return 0;
   if (n < 1024) n = 1024;
-  return make_layout(n).total;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) sms = v;
+  } else {
+    cudaGetLastError();
+  }
+  return make_layout(n, sms).total;
 }
 
 int vd_build(vd_ctx* ctx, const float* xyz, const float* weights, int64_t n, vd_box bbox, const vd_out* out,
@@ -448,7 +476,7 @@ int vd_build_batched(vd_ctx* ctx, const float* xyz, const float* weights, const 
     S.root = 0;
     S.weighted = weights ? (weighted ? (weighted[s] ? 1 : 0) : 1) : 0;
   }
-  // Morton codes of 18 bits per axis below a 10-bit set id
+  // 10-bit set id, 3-bit weight stratum, 17-bit Morton coordinates
   return run_forward(ctx, xyz, weights, (int)n, nsets, 54, out, (cudaStream_t)stream);
 }
 
@@ -462,6 +490,7 @@ int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroi
   cudaMemsetAsync(grad_sites, 0, sizeof(float) * 3 * (size_t)n, s);
   if (grad_weights) cudaMemsetAsync(grad_weights, 0, sizeof(float) * (size_t)n, s);
   cudaMemsetAsync(ctx->work + 2, 0, sizeof(int) * 3, s);
+  cudaMemsetAsync(&ctx->st->error, 0, sizeof(int), s);
   BackBuffers b;
   b.c = cell_buffers(ctx);
   b.inv_perm = ctx->inv_perm;
@@ -531,6 +560,9 @@ int vd_get_status(vd_ctx* ctx, vd_status* st) {
   st->nodes = d.nodes;
   st->vertex_tests = d.vertex_tests;
   st->new_vertices = d.new_vertices;
+  st->refined_vertices = d.refined_vertices;
+  st->refined_volumes = d.refined_volumes;
+  for (int k = 0; k < 4; k++) st->overflow_reason[k] = d.ovf_reason[k];
   return VD_OK;
 }
 

@@ -14,22 +14,80 @@
 // where M~ = int x~ dV and g~ = M~/V. Each cell is re-clipped from its
 // stored neighbour list (no traversal), its faces integrated by the same
 // fan tetrahedra as the forward pass, and the face terms scatter-added.
-#include "vd_clip.cuh"
+#include "vd_big.cuh"
 
 namespace vd {
 
 template <int VPL, int PCAP>
 struct BackSmem {
-  WarpSmem<VPL, PCAP> w;
+  WarpSmem<VPL, PCAP, 1> w;
   float acc[PCAP][10];  // per face: A, int y (3), int y y^T (6), y = x~ - c
 };
+
+// Scatter one site face's contribution (accumulators A = area, int y,
+// int y y^T about the vertex mean c) of cell i to the neighbour j, and add
+// the cell's own share to gpi / gwi.
+__device__ __forceinline__ void face_gradient(const float* A, float cx, float cy, float cz, float4 me, float4 qj,
+                                              int oj, float ap, float b0, float b1, float b2, float* gp, float* gw,
+                                              float& gpi0, float& gpi1, float& gpi2, float& gwi) {
+  float Ar = A[0];
+  float iy[3] = {A[1], A[2], A[3]};
+  float Syy[3][3] = {{A[4], A[7], A[8]}, {A[7], A[5], A[9]}, {A[8], A[9], A[6]}};
+  float cc[3] = {cx, cy, cz};
+  // shift the moments from the vertex mean c to the site p_i
+  float Am[3], St[3][3];
+#pragma unroll
+  for (int p = 0; p < 3; p++) Am[p] = Ar * cc[p] + iy[p];
+#pragma unroll
+  for (int p = 0; p < 3; p++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) St[p][r] = Ar * cc[p] * cc[r] + cc[p] * iy[r] + iy[p] * cc[r] + Syy[p][r];
+  float n[3] = {qj.x - me.x, qj.y - me.y, qj.z - me.z};
+  float D = sqrtf(fmaf(n[0], n[0], fmaf(n[1], n[1], n[2] * n[2])));
+  float iD = 1.0f / D;
+  float amb = Am[0] * b0 + Am[1] * b1 + Am[2] * b2;
+  float Sb[3];
+#pragma unroll
+  for (int p = 0; p < 3; p++) Sb[p] = St[p][0] * b0 + St[p][1] * b1 + St[p][2] * b2;
+#pragma unroll
+  for (int p = 0; p < 3; p++) {
+    float gj = (ap * (Ar * n[p] - Am[p]) + n[p] * amb - Sb[p]) * iD;
+    atomicAdd(&gp[3 * (size_t)oj + p], gj);
+  }
+  gpi0 += (ap * Am[0] + Sb[0]) * iD;
+  gpi1 += (ap * Am[1] + Sb[1]) * iD;
+  gpi2 += (ap * Am[2] + Sb[2]) * iD;
+  float gwc = (ap * Ar + amb) * 0.5f * iD;
+  gwi += gwc;
+  if (gw) atomicAdd(&gw[oj], -gwc);
+}
+
+// Triangle (g, a, b) of face f (unit normal nf), coordinates relative to
+// the vertex mean: add its area, first and second moments to A[0..9].
+__device__ __forceinline__ void face_accumulate(float* A, const float* g, const float* a, const float* b, float4 nf) {
+  float e1[3] = {a[0] - g[0], a[1] - g[1], a[2] - g[2]};
+  float e2[3] = {b[0] - g[0], b[1] - g[1], b[2] - g[2]};
+  float cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2], cr2 = e1[0] * e2[1] - e1[1] * e2[0];
+  float al = 0.5f * (cr0 * nf.x + cr1 * nf.y + cr2 * nf.z);
+  float s[3] = {g[0] + a[0] + b[0], g[1] + a[1] + b[1], g[2] + a[2] + b[2]};
+  atomicAdd(&A[0], al);
+#pragma unroll
+  for (int k = 0; k < 3; k++) atomicAdd(&A[1 + k], al * s[k] * (1.0f / 3.0f));
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    int p = ii[k], r = jj[k];
+    float m2 = g[p] * g[r] + a[p] * a[r] + b[p] * b[r] + s[p] * s[r];
+    atomicAdd(&A[4 + k], al * m2 * (1.0f / 12.0f));
+  }
+}
 
 template <int VPL, int PCAP, int QPL>
 __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si, Counters& ct) {
   using C = Cell<VPL, PCAP, QPL>;
   constexpr int NPW = C::NPW;
   const CellBuffers& P = B.c;
-  WarpSmem<VPL, PCAP>& S = SM.w;
+  WarpSmem<VPL, PCAP, 1>& S = SM.w;
   const unsigned lane = lane_id();
   C c;
   c.me = P.sites[si];
@@ -45,7 +103,8 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
   if (cnt <= 0) return true;  // empty cell (or no site faces): no moving face
   init_cell(c, S);
   const int slot = P.ovf_slot[orig_i];
-  const int* row = slot >= 0 ? P.scratch_big + (size_t)slot * P.stride_big : P.scratch + (size_t)orig_i * P.stride;
+  if (slot >= 0) return false;  // a long neighbour list: the large-cell adjoint
+  const int* row = P.scratch + (size_t)orig_i * P.stride;
   for (int c0 = 0; c0 < cnt; c0 += 32) {
     int t = c0 + (int)lane;
     bool keep = t < cnt;
@@ -110,22 +169,7 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
     My += det * (g[1] + a[1] + b[1]);
     Mz += det * (g[2] + a[2] + b[2]);
     if (S.pid[fy] < 0) continue;  // box faces do not move
-    float e1[3] = {a[0] - g[0], a[1] - g[1], a[2] - g[2]};
-    float e2[3] = {b[0] - g[0], b[1] - g[1], b[2] - g[2]};
-    float cr0 = e1[1] * e2[2] - e1[2] * e2[1], cr1 = e1[2] * e2[0] - e1[0] * e2[2], cr2 = e1[0] * e2[1] - e1[1] * e2[0];
-    float al = 0.5f * (cr0 * pf.x + cr1 * pf.y + cr2 * pf.z);
-    float s[3] = {g[0] + a[0] + b[0], g[1] + a[1] + b[1], g[2] + a[2] + b[2]};
-    float* A = SM.acc[fy];
-    atomicAdd(&A[0], al);
-#pragma unroll
-    for (int k = 0; k < 3; k++) atomicAdd(&A[1 + k], al * s[k] * (1.0f / 3.0f));
-    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      int p = ii[k], r = jj[k];
-      float m2 = g[p] * g[r] + a[p] * a[r] + b[p] * b[r] + s[p] * s[r];
-      atomicAdd(&A[4 + k], al * m2 * (1.0f / 12.0f));
-    }
+    face_accumulate(SM.acc[fy], g, a, b, pf);
   }
   V = warp_sumf(V) * (1.0f / 6.0f);
   Mx = warp_sumf(Mx) * (1.0f / 24.0f);
@@ -149,42 +193,9 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
   for (int w = 0; w < NPW; w++) {
     int f = 32 * w + (int)lane;
     if (!((alive[w] >> lane) & 1u) || S.pid[f] < 0) continue;
-    const float* A = SM.acc[f];
-    float Ar = A[0];
-    float iy[3] = {A[1], A[2], A[3]};
-    float Syy[3][3] = {{A[4], A[7], A[8]}, {A[7], A[5], A[9]}, {A[8], A[9], A[6]}};
-    float cc[3] = {cx, cy, cz};
-    // shift the moments from the vertex mean c to the site p_i
-    float Am[3], St[3][3];
-#pragma unroll
-    for (int p = 0; p < 3; p++) Am[p] = Ar * cc[p] + iy[p];
-#pragma unroll
-    for (int p = 0; p < 3; p++)
-#pragma unroll
-      for (int r = 0; r < 3; r++) St[p][r] = Ar * cc[p] * cc[r] + cc[p] * iy[r] + iy[p] * cc[r] + Syy[p][r];
     int js = S.pid[f];
-    float4 qj = P.sites[js];
-    float n[3] = {qj.x - c.me.x, qj.y - c.me.y, qj.z - c.me.z};
-    float D = sqrtf(fmaf(n[0], n[0], fmaf(n[1], n[1], n[2] * n[2])));
-    float iD = 1.0f / D;
-    float bb[3] = {b0, b1, b2};
-    float amb = Am[0] * b0 + Am[1] * b1 + Am[2] * b2;
-    float Sb[3];
-#pragma unroll
-    for (int p = 0; p < 3; p++) Sb[p] = St[p][0] * b0 + St[p][1] * b1 + St[p][2] * b2;
-    int oj = P.perm[js];
-#pragma unroll
-    for (int p = 0; p < 3; p++) {
-      float gj = (ap * (Ar * n[p] - Am[p]) + n[p] * amb - Sb[p]) * iD;
-      atomicAdd(&B.gp[3 * (size_t)oj + p], gj);
-    }
-    gpi0 += (ap * Am[0] + Sb[0]) * iD;
-    gpi1 += (ap * Am[1] + Sb[1]) * iD;
-    gpi2 += (ap * Am[2] + Sb[2]) * iD;
-    float gwc = (ap * Ar + amb) * 0.5f * iD;
-    gwi += gwc;
-    if (B.gw) atomicAdd(&B.gw[oj], -gwc);
-    (void)bb;
+    face_gradient(SM.acc[f], cx, cy, cz, c.me, P.sites[js], P.perm[js], ap, b0, b1, b2, B.gp, B.gw, gpi0, gpi1,
+                  gpi2, gwi);
   }
   gpi0 = warp_sumf(gpi0);
   gpi1 = warp_sumf(gpi1);
@@ -200,33 +211,7 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
   return true;
 }
 
-template <int VPL, int PCAP, int QPL, bool BIG>
-__global__ void back_kernel(BackBuffers B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BackSmem<VPL, PCAP>* Sw = reinterpret_cast<BackSmem<VPL, PCAP>*>(smem_raw);
-  BackSmem<VPL, PCAP>& S = Sw[threadIdx.x >> 5];
-  const unsigned lane = lane_id();
-  Counters ct = {0, 0, 0, 0, 0, 0, 0};
-  const int total = BIG ? min(*B.list_count, B.list_cap) : B.c.n;
-  while (true) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&B.work[BIG ? 1 : 0], 1);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= total) break;
-    int si = BIG ? B.list[item] : item;
-    bool ok = back_cell<VPL, PCAP, QPL>(B, S, si, ct);
-    if (!ok && lane == 0) {
-      if (BIG) {
-        set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
-      } else {
-        int k = atomicAdd(B.list_count, 1);
-        if (k < B.list_cap)
-          B.list[k] = si;
-        else
-          set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
-      }
-    }
-  }
+__device__ inline void flush_back(const BackBuffers& B, const Counters& ct, unsigned lane) {
   long long f64 = ct.fp64, f64a = ct.fp64amb;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -239,25 +224,180 @@ __global__ void back_kernel(BackBuffers B) {
   }
 }
 
-template <int VPL, int PCAP, int QPL, bool BIG>
-static cudaError_t launch_back_variant(const BackBuffers& b, int num_sms, int wpb, int grid_override,
-                                       cudaStream_t s) {
-  size_t smem = sizeof(BackSmem<VPL, PCAP>) * (size_t)wpb;
-  auto kern = back_kernel<VPL, PCAP, QPL, BIG>;
+template <int VPL, int PCAP, int QPL>
+__global__ void back_kernel(BackBuffers B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BackSmem<VPL, PCAP>* Sw = reinterpret_cast<BackSmem<VPL, PCAP>*>(smem_raw);
+  BackSmem<VPL, PCAP>& S = Sw[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  Counters ct = {};
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&B.work[0], 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= B.c.n) break;
+    if (!back_cell<VPL, PCAP, QPL>(B, S, item, ct) && lane == 0) {
+      int k = atomicAdd(B.list_count, 1);
+      if (k < B.list_cap)
+        B.list[k] = item;
+      else
+        set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
+    }
+  }
+  flush_back(B, ct, lane);
+}
+
+// ---------------------------------------------------------------- large cells
+
+__device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, Counters& ct) {
+  const CellBuffers& P = B.c;
+  const unsigned lane = lane_id();
+  BigCell c;
+  c.me = P.sites[si];
+  const int orig_i = P.perm[si];
+  const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
+  const SetInfo& SI = P.sets[set];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c.lo[k] = SI.lo[k];
+    c.hi[k] = SI.hi[k];
+  }
+  const int cnt = P.counts[orig_i];
+  if (cnt <= 0) return true;
+  big_init(c, A);
+  const int slot = P.ovf_slot[orig_i];
+  const int* row = slot >= 0 ? P.pool + slot : P.scratch + (size_t)orig_i * P.stride;
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    int t = c0 + (int)lane;
+    bool keep = t < cnt;
+    int j = 0;
+    PlaneT<float> H;
+    H.nx = H.ny = H.nz = H.b = H.e = 0.f;
+    float dkey = INFINITY;
+    if (keep) {
+      j = B.inv_perm[row[t] + SI.first];
+      float4 q = P.sites[j];
+      H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+      dkey = H.b;
+    }
+    uint32_t km = __ballot_sync(FULL, keep);
+    while (km) {
+      uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
+      uint32_t mn = __reduce_min_sync(FULL, key);
+      int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
+      PlaneT<float> Hb;
+      Hb.nx = __shfl_sync(FULL, H.nx, src);
+      Hb.ny = __shfl_sync(FULL, H.ny, src);
+      Hb.nz = __shfl_sync(FULL, H.nz, src);
+      Hb.b = __shfl_sync(FULL, H.b, src);
+      Hb.e = __shfl_sync(FULL, H.e, src);
+      int hj = __shfl_sync(FULL, j, src);
+      if ((int)lane == src) keep = false;
+      km &= ~(1u << src);
+      int rc = big_clip(c, A, Hb, hj, P.sites, ct, false);
+      if (rc == CLIP_OVERFLOW) return false;
+      if (rc == CLIP_EMPTY) return true;
+    }
+  }
+  big_mark_planes(c, A);
+  const uint32_t hmask = big_hash_vertices(c, A);
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = (int)lane; i < c.nv; i += 32) {
+    float4 v = A.vp[i];
+    sx += v.x;
+    sy += v.y;
+    sz += v.z;
+  }
+  const float cx = warp_sumf(sx) / c.nv, cy = warp_sumf(sy) / c.nv, cz = warp_sumf(sz) / c.nv;
+  for (int q = (int)lane; q < 10 * c.npl; q += 32) A.acc[q] = 0.f;
+  __syncwarp();
+  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
+  for (int it = (int)lane; it < 3 * c.nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t q = bpair(A.vt[t], rho);
+    uint32_t fy = q >> 16;
+    int u = hash_find(A, brev(q), hmask);
+    if (u < 0) continue;
+    float4 pf = A.pl[fy];
+    float hgt = fmaf(pf.x, cx, fmaf(pf.y, cy, fmaf(pf.z, cz, -pf.w)));
+    float g[3] = {-hgt * pf.x, -hgt * pf.y, -hgt * pf.z};
+    float4 va = A.vp[t], vb = A.vp[u];
+    float a[3] = {va.x - cx, va.y - cy, va.z - cz};
+    float b[3] = {vb.x - cx, vb.y - cy, vb.z - cz};
+    float det = g[0] * (a[1] * b[2] - a[2] * b[1]) + g[1] * (a[2] * b[0] - a[0] * b[2]) +
+                g[2] * (a[0] * b[1] - a[1] * b[0]);
+    V += det;
+    Mx += det * (g[0] + a[0] + b[0]);
+    My += det * (g[1] + a[1] + b[1]);
+    Mz += det * (g[2] + a[2] + b[2]);
+    if (A.pid[fy] < 0) continue;
+    face_accumulate(A.acc + 10 * (size_t)fy, g, a, b, pf);
+  }
+  V = warp_sumf(V) * (1.0f / 6.0f);
+  Mx = warp_sumf(Mx) * (1.0f / 24.0f);
+  My = warp_sumf(My) * (1.0f / 24.0f);
+  Mz = warp_sumf(Mz) * (1.0f / 24.0f);
+  __syncwarp();
+  if (!(V > 0.f)) return true;
+  const float gx = cx + Mx / V, gy = cy + My / V, gz = cz + Mz / V;
+  float gv = B.gvol ? B.gvol[orig_i] : 0.f;
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+  if (B.gcen) {
+    d0 = B.gcen[3 * (size_t)orig_i];
+    d1 = B.gcen[3 * (size_t)orig_i + 1];
+    d2 = B.gcen[3 * (size_t)orig_i + 2];
+  }
+  const float b0 = d0 / V, b1 = d1 / V, b2 = d2 / V;
+  const float ap = gv - (b0 * gx + b1 * gy + b2 * gz);
+  float gpi0 = 0.f, gpi1 = 0.f, gpi2 = 0.f, gwi = 0.f;
+  for (int f = (int)lane; f < c.npl; f += 32) {
+    if (!A.flag[f] || A.pid[f] < 0) continue;
+    int js = A.pid[f];
+    face_gradient(A.acc + 10 * (size_t)f, cx, cy, cz, c.me, P.sites[js], P.perm[js], ap, b0, b1, b2, B.gp, B.gw,
+                  gpi0, gpi1, gpi2, gwi);
+  }
+  gpi0 = warp_sumf(gpi0);
+  gpi1 = warp_sumf(gpi1);
+  gpi2 = warp_sumf(gpi2);
+  gwi = warp_sumf(gwi);
+  if (lane == 0) {
+    atomicAdd(&B.gp[3 * (size_t)orig_i], gpi0);
+    atomicAdd(&B.gp[3 * (size_t)orig_i + 1], gpi1);
+    atomicAdd(&B.gp[3 * (size_t)orig_i + 2], gpi2);
+    if (B.gw) atomicAdd(&B.gw[orig_i], gwi);
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void big_back_kernel(BackBuffers B) {
+  const unsigned lane = lane_id();
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const BigArena A = big_arena(B.c.arena, slot);
+  Counters ct = {};
+  const int total = min(*B.list_count, B.list_cap);
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&B.work[1], 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= total) break;
+    if (!big_back_cell(B, A, B.list[item], ct) && lane == 0) set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
+  }
+  flush_back(B, ct, lane);
+}
+
+cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s) {
+  const int wpb = 4;
+  size_t smem = sizeof(BackSmem<4, 128>) * (size_t)wpb;
+  auto kern = back_kernel<4, 128, 1>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int occ = 0;
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * wpb, smem);
   if (err != cudaSuccess) return err;
-  int grid = grid_override > 0 ? grid_override : num_sms * (occ > 0 ? occ : 1);
-  kern<<<grid, 32 * wpb, smem, s>>>(b);
+  kern<<<num_sms * (occ > 0 ? occ : 1), 32 * wpb, smem, s>>>(b);
+  big_back_kernel<<<num_sms, 32 * kBigWarpsPerBlock, 0, s>>>(b);
   return cudaGetLastError();
-}
-
-cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s) {
-  cudaError_t err = launch_back_variant<4, 64, 1, false>(b, num_sms, 4, 0, s);
-  if (err != cudaSuccess) return err;
-  return launch_back_variant<8, 192, 1, true>(b, num_sms, 4, num_sms * 2, s);
 }
 
 __global__ void inverse_perm_kernel(const int* __restrict__ perm, int n, int* __restrict__ inv) {

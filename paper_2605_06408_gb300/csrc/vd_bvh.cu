@@ -10,7 +10,8 @@ namespace vd {
 // ---------------------------------------------------------------- Morton keys
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v) {
-  // spread the low 21 bits of v so that bit k lands on bit 3k
+  // spread the low 21 bits of v so that bit k lands on bit 3k (callers use
+  // at most 20 bits per axis)
   uint64_t x = v & 0x1fffffu;
   x = (x | (x << 32)) & 0x1f00000000ffffull;
   x = (x | (x << 16)) & 0x1f0000ff0000ffull;
@@ -32,11 +33,55 @@ __device__ __forceinline__ int find_set(const SetInfo* sets, int nsets, int i) {
   return lo;
 }
 
+// Range of the weights of weighted sets (orderable-uint min / max).
+__global__ void weight_range_kernel(const float* __restrict__ w, int n, const SetInfo* __restrict__ sets, int nsets,
+                                    unsigned* __restrict__ wr) {
+  uint32_t mn = 0xffffffffu, mx = 0u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int s = nsets > 1 ? find_set(sets, nsets, i) : 0;
+    if (!sets[s].weighted || !isfinite(w[i])) continue;
+    uint32_t o = f2o(w[i]);
+    mn = min(mn, o);
+    mx = max(mx, o);
+  }
+  mn = __reduce_min_sync(FULL, mn);
+  mx = __reduce_max_sync(FULL, mx);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&wr[0], mn);
+    atomicMax(&wr[1], mx);
+  }
+}
+
+cudaError_t launch_weight_range(const float* w, int n, const SetInfo* sets, int nsets, unsigned* wr,
+                                cudaStream_t s) {
+  cudaMemsetAsync(wr, 0xff, sizeof(unsigned), s);
+  cudaMemsetAsync(wr + 1, 0, sizeof(unsigned), s);
+  if (!w) return cudaGetLastError();
+  int blocks = min((n + 255) / 256, 1024);
+  weight_range_kernel<<<blocks, 256, 0, s>>>(w, n, sets, nsets, wr);
+  return cudaGetLastError();
+}
+
+// Weight stratum of a site (a performance device only; any partition
+// gives the same cells): with o = w - w_min and O = w_max - w_min, bin 7
+// holds o in (O/4, O], bin 6 (O/16, O/4], ... bin 0 everything below.
+// Sorting by (bin, Morton) puts each stratum in its own subtrees, so a
+// node's maximum weight -- the w_max of the node bound of Sec. 4.2.2 --
+// is within a factor 4 of its sites' weights instead of the global maximum.
+__device__ __forceinline__ uint32_t weight_bin(float w, float wmin, float wmax) {
+  float O = wmax - wmin, o = w - wmin;
+  if (!(O > 0.f) || !(o > 0.f)) return 0u;
+  int k = (int)(0.5f * log2f(O / o));
+  return (uint32_t)max(0, 7 - k);
+}
+
 __global__ void pack_keys_kernel(const float* __restrict__ xyz, const float* __restrict__ w, int n,
-                                 const SetInfo* __restrict__ sets, int nsets, int set_shift,
-                                 uint64_t* __restrict__ keys, int* __restrict__ vals, DevStatus* st) {
-  const int bits = set_shift / 3;
+                                 const SetInfo* __restrict__ sets, int nsets, int set_shift, int bin_shift,
+                                 const unsigned* __restrict__ wr, uint64_t* __restrict__ keys, int* __restrict__ vals,
+                                 DevStatus* st) {
+  const int bits = bin_shift / 3;
   const float scale = (float)(1u << bits);
+  const float wmin = o2f(wr[0]), wmax = o2f(wr[1]);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     int s = nsets > 1 ? find_set(sets, nsets, i) : 0;
@@ -54,18 +99,19 @@ __global__ void pack_keys_kernel(const float* __restrict__ xyz, const float* __r
       q[k] = (uint32_t)fminf(v, scale - 1.0f);
     }
     uint64_t code = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
-    keys[i] = ((uint64_t)s << set_shift) | code;
+    uint32_t bin = (w && S.weighted && wr[0] <= wr[1]) ? weight_bin(w[i], wmin, wmax) : 0u;
+    keys[i] = ((uint64_t)s << set_shift) | ((uint64_t)bin << bin_shift) | code;
     vals[i] = i;
   }
 }
 
-cudaError_t launch_pack_keys(const float* xyz, const float* w, int n, const SetInfo* sets, int nsets,
-                             const int* /*unused*/, int set_shift, uint64_t* keys, int* vals, DevStatus* st,
+cudaError_t launch_pack_keys(const float* xyz, const float* w, int n, const SetInfo* sets, int nsets, int set_shift,
+                             int bin_shift, const unsigned* wr, uint64_t* keys, int* vals, DevStatus* st,
                              cudaStream_t s) {
   int threads = 256;
   int blocks = (n + threads - 1) / threads;
   if (blocks > 4096) blocks = 4096;
-  pack_keys_kernel<<<blocks, threads, 0, s>>>(xyz, w, n, sets, nsets, set_shift, keys, vals, st);
+  pack_keys_kernel<<<blocks, threads, 0, s>>>(xyz, w, n, sets, nsets, set_shift, bin_shift, wr, keys, vals, st);
   return cudaGetLastError();
 }
 
@@ -198,6 +244,34 @@ cudaError_t launch_gather_sites(const float* xyz, const float* w, const int* per
   int threads = 256;
   int blocks = min((n + threads - 1) / threads, 4096);
   gather_sites_kernel<<<blocks, threads, 0, s>>>(xyz, w, perm, n, sets, keys, set_shift, nsets, sites);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- duplicates
+// Sites at exactly the same position share a Morton key and are adjacent
+// after the sort. Among them the larger weight, then the lower original
+// index, keeps its cell; every other one has an empty cell, and its
+// half-space is implied by the winner's, so it is never a candidate.
+__global__ void mark_losers_kernel(const uint64_t* __restrict__ keys, const float4* __restrict__ sites,
+                                   const int* __restrict__ perm, int n, unsigned char* __restrict__ loser) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    uint64_t key = keys[k];
+    float4 p = sites[k];
+    bool lose = false;
+    for (int dir = -1; dir <= 1 && !lose; dir += 2)
+      for (int m = k + dir; m >= 0 && m < n && keys[m] == key && !lose; m += dir) {
+        float4 q = sites[m];
+        if (q.x == p.x && q.y == p.y && q.z == p.z)
+          lose = q.w > p.w || (q.w == p.w && perm[m] < perm[k]);
+      }
+    loser[k] = lose ? 1 : 0;
+  }
+}
+
+cudaError_t launch_mark_losers(const uint64_t* keys, const float4* sites, const int* perm, int n,
+                               unsigned char* loser, cudaStream_t s) {
+  int blocks = min((n + 255) / 256, 4096);
+  mark_losers_kernel<<<blocks, 256, 0, s>>>(keys, sites, perm, n, loser);
   return cudaGetLastError();
 }
 

@@ -21,45 +21,21 @@
 // bound of zero is re-evaluated in FP64 from the original inputs.
 #include <functional>
 
-#include "vd_clip.cuh"
+#include "vd_big.cuh"
 
 namespace vd {
-
-// Candidate pre-test of Sec. 4.2.1: the plane n.x <= beta can cut the cell
-// only if it cuts the cell's AABB, i.e. n.c_o > beta for the AABB corner c_o
-// of n's octant (the exact support of the box in direction n; the paper's
-// per-octant corner distance |c_o| bounds it from above).
-__device__ __forceinline__ bool candidate_test(float nx, float ny, float nz, float nn, float beta, float wi,
-                                               float wj, const float* alo, const float* ahi, int cull_mode) {
-  if (cull_mode == 2) return true;
-  float n[3] = {nx, ny, nz};
-  float pad = 0.5f * (nn + fabsf(wi) + fabsf(wj));
-  if (cull_mode == 1) {
-    float R = sqrtf(dir_radius2(0, alo, ahi, 1));
-    float len = sqrtf(nn);
-    pad = kCullPad * (pad + len * R);
-    return len * R * (1.0f + kCullPad) > beta - pad;
-  }
-  float sup = 0.0f, mag = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    float t = n[k] > 0.0f ? n[k] * ahi[k] : (n[k] < 0.0f ? n[k] * alo[k] : 0.0f);
-    sup += t;
-    mag += fabsf(t);
-  }
-  return sup > beta - kCullPad * (pad + mag);
-}
 
 // Process the sites of one leaf: pre-cull all of them in parallel, then
 // clip with the survivors in ascending power distance d_ij (Eq. 2).
 template <int VPL, int PCAP, int QPL>
-__device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, int ref, int si, int orig_i,
+__device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int ref, int si, int orig_i,
                             const CellBuffers& P, Counters& ct) {
   const unsigned lane = lane_id();
   const bool counters = P.cfg.counters != 0;
   int first = leaf_first(ref), cnt = leaf_count(ref);
   int j = first + (int)lane;
   bool act = (int)lane < cnt && j != si;
+  if (act) act = P.loser[j] == 0;
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) q = P.sites[j];
   PlaneT<float> H;
@@ -72,7 +48,7 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, int
     dup = nx == 0.0f && ny == 0.0f && nz == 0.0f;
     if (!dup) {
       float beta = 0.5f * (nn + (c.me.w - q.w));
-      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, P.cfg.cull_mode);
+      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, P.cfg.cull_mode);
       if (keep) {
         H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
         dkey = H.b;
@@ -99,7 +75,7 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, int
     if ((int)lane == src) keep = false;
     km &= ~(1u << src);
     int rc = clip_cell(c, S, Hb, first + src, P.sites, ct, counters);
-    if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW) return rc;
+    if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) return rc;
     if (rc == CLIP_DONE) {
       c.dirty = true;
       if (counters) ct.clips++;
@@ -110,8 +86,8 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, int
 
 // Build one cell and write its outputs. Returns false on overflow.
 template <int VPL, int PCAP, int QPL>
-__device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si, int* row, Counters& ct,
-                           long long& empties) {
+__device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, int si, int* row, Counters& ct,
+                           long long& empties, int& reason) {
   using C = Cell<VPL, PCAP, QPL>;
   constexpr int NPW = C::NPW;
   const unsigned lane = lane_id(), lt = lanemask_lt();
@@ -119,6 +95,17 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
   C c;
   c.me = P.sites[si];
   const int orig_i = P.perm[si];
+  if (P.loser[si]) {  // an exact duplicate site owns this position
+    if (lane == 0) {
+      P.counts[orig_i] = 0;
+      P.vol[orig_i] = 0.0f;
+      P.cen[3 * (size_t)orig_i] = c.me.x;
+      P.cen[3 * (size_t)orig_i + 1] = c.me.y;
+      P.cen[3 * (size_t)orig_i + 2] = c.me.z;
+    }
+    empties++;
+    return true;
+  }
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
 #pragma unroll
@@ -141,7 +128,8 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
           empty = true;
           break;
         }
-        if (rc == CLIP_OVERFLOW) {
+        if (rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) {
+          reason = rc == CLIP_OVERFLOW ? OVF_VERTICES : OVF_PLANES;
           overflow = true;
           break;
         }
@@ -162,7 +150,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
         float lb = 0.f, key = 0.f;
         int occ = 0;
         bool keep = false;
-        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, c.alo, c.ahi, cull, lb, occ, key);
+        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, c.alo, c.ahi, c.sc, c.srad, cull, lb, occ, key);
         int myref = __float_as_int(hi.w);
         bool k0 = __shfl_sync(FULL, keep, 0), k1 = __shfl_sync(FULL, keep, 2);
         float key0 = __shfl_sync(FULL, key, 0), key1 = __shfl_sync(FULL, key, 2);
@@ -174,7 +162,8 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
           float flb = __shfl_sync(FULL, lb, fsrc);
           int focc = __shfl_sync(FULL, occ, fsrc);
           cur = near0 ? r0 : r1;
-          if (!queue_push(c, flb, near0 ? r1 : r0, focc)) {
+          if (!queue_push(c, S, flb, near0 ? r1 : r0, focc)) {
+            reason = OVF_QUEUE;
             overflow = true;
             break;
           }
@@ -188,7 +177,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
       }
       if (have) continue;
     }
-    if (!queue_pop(c, cull, trav, cur)) break;
+    if (!queue_pop(c, S, cull, trav, cur)) break;
     have = true;
   }
   if (overflow) return false;
@@ -223,6 +212,10 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
     nvals += __popc(mk);
   }
   __syncwarp();
+  if (nvals > P.stride) {  // more neighbours than a fast-path row holds
+    reason = OVF_NEIGHBORS;
+    return false;
+  }
   for (int t = (int)lane; t < nvals; t += 32) {
     int v = (int)S.otri[t];
     int rank = 0;
@@ -233,7 +226,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
   // edge v -> w of face f (w = the other end of the edge), g_f = the foot of
   // c on plane f; c = vertex mean
   float cx = sx / nv, cy = sy / nv, cz = sz / nv;
-  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
+  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, Sabs = 0.f, emax = 0.f;
   for (int it = (int)lane; it < 3 * nv; it += 32) {
     int t = it / 3, rho = it % 3;
     uint32_t T = S.nvt[t];
@@ -255,86 +248,68 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP>& S, int si,
     Mx += det * (gx + ax + bx);
     My += det * (gy + ay + by);
     Mz += det * (gz + az + bz);
+    float e1x = ax - gx, e1y = ay - gy, e1z = az - gz, e2x = bx - gx, e2y = by - gy, e2z = bz - gz;
+    float crx = e1y * e2z - e1z * e2y, cry = e1z * e2x - e1x * e2z, crz = e1x * e2y - e1y * e2x;
+    Sabs += sqrtf(crx * crx + cry * cry + crz * crz);
+    emax = fmaxf(emax, a.w);
   }
   V = warp_sumf(V) * (1.0f / 6.0f);
   Mx = warp_sumf(Mx) * (1.0f / 24.0f);
   My = warp_sumf(My) * (1.0f / 24.0f);
   Mz = warp_sumf(Mz) * (1.0f / 24.0f);
+  Sabs = warp_sumf(Sabs) * 0.5f;
+  emax = warp_maxf(emax);
+  float L = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; k++) L += fmaxf(c.alo[k] * c.alo[k], c.ahi[k] * c.ahi[k]);
+  L = sqrtf(L);
+  double ox = cx, oy = cy, oz = cz;
+  double Vd = V;
+  if (volume_needs_fp64(V, L, Sabs, emax)) {
+    double Mxd, Myd, Mzd;
+    volume_fp64(S, nv, c.me, c.lo, c.hi, P.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
+    if (Vd > 0.0) {
+      ox += Mxd / Vd;
+      oy += Myd / Vd;
+      oz += Mzd / Vd;
+    }
+    ct.refvol++;
+  } else if (V > 0.0f) {
+    ox += Mx / V;
+    oy += My / V;
+    oz += Mz / V;
+  }
   if (lane == 0) {
     P.counts[orig_i] = nvals;
-    vol[orig_i] = V;
-    float ox = cx, oy = cy, oz = cz;
-    if (V > 0.0f) {
-      ox += Mx / V;
-      oy += My / V;
-      oz += Mz / V;
-    }
-    cen[3 * (size_t)orig_i] = c.me.x + ox;
-    cen[3 * (size_t)orig_i + 1] = c.me.y + oy;
-    cen[3 * (size_t)orig_i + 2] = c.me.z + oz;
+    vol[orig_i] = (float)Vd;
+    cen[3 * (size_t)orig_i] = (float)((double)c.me.x + ox);
+    cen[3 * (size_t)orig_i + 1] = (float)((double)c.me.y + oy);
+    cen[3 * (size_t)orig_i + 2] = (float)((double)c.me.z + oz);
   }
   __syncwarp();
   return true;
 }
 
-template <int VPL, int PCAP, int QPL, bool BIG>
-__global__ void cells_kernel(CellBuffers P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem<VPL, PCAP>* Sw = reinterpret_cast<WarpSmem<VPL, PCAP>*>(smem_raw);
-  WarpSmem<VPL, PCAP>& S = Sw[threadIdx.x >> 5];
-  const unsigned lane = lane_id();
-  Counters ct = {0, 0, 0, 0, 0, 0, 0};
-  long long empties = 0, overflows = 0, failed = 0;
-  const int total = BIG ? min(P.st->ovf_count, P.ovf_cap) : P.n;
-  while (true) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&P.work[BIG ? 1 : 0], 1);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= total) break;
-    int si = BIG ? P.ovf_list[item] : item;
-    int orig = P.perm[si];
-    int* row = BIG ? P.scratch_big + (size_t)item * P.stride_big : P.scratch + (size_t)orig * P.stride;
-    bool ok = build_cell<VPL, PCAP, QPL>(P, S, si, row, ct, empties);
-    if (!ok) {
-      if (BIG) {
-        failed++;
-        if (lane == 0) {
-          P.counts[orig] = 0;
-          P.vol[orig] = __int_as_float(0x7fc00000);
-          set_error(P.st, VD_ERR_CELL_OVERFLOW);
-        }
-      } else {
-        overflows++;
-        if (lane == 0) {
-          int slot = atomicAdd(&P.st->ovf_count, 1);
-          if (slot < P.ovf_cap) {
-            P.ovf_list[slot] = si;
-          } else {
-            P.counts[orig] = 0;
-            P.vol[orig] = __int_as_float(0x7fc00000);
-            set_error(P.st, VD_ERR_CELL_OVERFLOW);
-          }
-        }
-      }
-    } else if (BIG && lane == 0) {
-      P.ovf_slot[orig] = item;
-    }
-  }
+__device__ inline void flush_counters(const CellBuffers& P, const Counters& ct, unsigned lane, long long empties,
+                                      long long overflows, long long failed) {
   if (lane == 0) {
     if (empties) atomicAdd((unsigned long long*)&P.st->empty_cells, (unsigned long long)empties);
     if (overflows) atomicAdd((unsigned long long*)&P.st->overflow_cells, (unsigned long long)overflows);
     if (failed) atomicAdd((unsigned long long*)&P.st->failed_cells, (unsigned long long)failed);
   }
-  // per-lane counters (FP64 re-evaluations happen on individual lanes)
-  long long f64 = ct.fp64, f64a = ct.fp64amb;
+  // FP64 re-evaluations happen on individual lanes
+  long long f64 = ct.fp64, f64a = ct.fp64amb, rv = ct.refv;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     f64 += __shfl_xor_sync(FULL, f64, o);
     f64a += __shfl_xor_sync(FULL, f64a, o);
+    rv += __shfl_xor_sync(FULL, rv, o);
   }
   if (lane == 0) {
     if (f64) atomicAdd((unsigned long long*)&P.st->fp64_fallbacks, (unsigned long long)f64);
     if (f64a) atomicAdd((unsigned long long*)&P.st->fp64_ambiguous, (unsigned long long)f64a);
+    if (rv) atomicAdd((unsigned long long*)&P.st->refined_vertices, (unsigned long long)rv);
+    if (ct.refvol) atomicAdd((unsigned long long*)&P.st->refined_volumes, (unsigned long long)ct.refvol);
     if (P.cfg.counters) {
       atomicAdd((unsigned long long*)&P.st->candidates, (unsigned long long)ct.cand);
       atomicAdd((unsigned long long*)&P.st->clips, (unsigned long long)ct.clips);
@@ -345,41 +320,416 @@ __global__ void cells_kernel(CellBuffers P) {
   }
 }
 
-template <int VPL, int PCAP, int QPL, bool BIG>
-static cudaError_t launch_variant(const CellBuffers& c, int num_sms, int grid_override, cudaStream_t s) {
+template <int VPL, int PCAP, int QPL>
+__global__ void cells_kernel(CellBuffers P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<VPL, PCAP, QPL>* Sw = reinterpret_cast<WarpSmem<VPL, PCAP, QPL>*>(smem_raw);
+  WarpSmem<VPL, PCAP, QPL>& S = Sw[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  Counters ct = {};
+  long long empties = 0, overflows = 0;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&P.work[0], 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= P.n) break;
+    const int si = item;
+    const int orig = P.perm[si];
+    int* row = P.scratch + (size_t)orig * P.stride;
+    int reason = 0;
+    if (!build_cell<VPL, PCAP, QPL>(P, S, si, row, ct, empties, reason)) {
+      overflows++;
+      if (lane == 0) atomicAdd((unsigned long long*)&P.st->ovf_reason[reason], 1ull);
+      if (lane == 0) {
+        int slot = atomicAdd(&P.st->ovf_count, 1);
+        if (slot < P.ovf_cap) {
+          P.ovf_list[slot] = si;
+        } else {
+          P.counts[orig] = 0;
+          P.vol[orig] = __int_as_float(0x7fc00000);
+          set_error(P.st, VD_ERR_CELL_OVERFLOW);
+        }
+      }
+    }
+  }
+  flush_counters(P, ct, lane, empties, overflows, 0);
+}
+
+// ---------------------------------------------------------------- large cells
+
+__device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig_i, const CellBuffers& P,
+                        Counters& ct) {
+  const unsigned lane = lane_id();
+  const bool counters = P.cfg.counters != 0;
+  int first = leaf_first(ref), cnt = leaf_count(ref);
+  int j = first + (int)lane;
+  bool act = (int)lane < cnt && j != si;
+  if (act) act = P.loser[j] == 0;
+  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (act) q = P.sites[j];
+  PlaneT<float> H;
+  H.nx = H.ny = H.nz = H.b = H.e = 0.0f;
+  bool keep = false, dup = false;
+  float dkey = INFINITY;
+  if (act) {
+    float nx = q.x - c.me.x, ny = q.y - c.me.y, nz = q.z - c.me.z;
+    float nn = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    dup = nx == 0.0f && ny == 0.0f && nz == 0.0f;
+    if (!dup) {
+      float beta = 0.5f * (nn + (c.me.w - q.w));
+      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, P.cfg.cull_mode);
+      if (keep) {
+        H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+        dkey = H.b;
+      }
+    }
+  }
+  if (__any_sync(FULL, dup)) {
+    bool beats = dup && (q.w > c.me.w || (q.w == c.me.w && P.perm[j] < orig_i));
+    if (__any_sync(FULL, beats)) return CLIP_EMPTY;
+  }
+  uint32_t km = __ballot_sync(FULL, keep);
+  if (counters) ct.cand += __popc(km);
+  while (km) {
+    uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
+    uint32_t mn = __reduce_min_sync(FULL, key);
+    int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
+    PlaneT<float> Hb;
+    Hb.nx = __shfl_sync(FULL, H.nx, src);
+    Hb.ny = __shfl_sync(FULL, H.ny, src);
+    Hb.nz = __shfl_sync(FULL, H.nz, src);
+    Hb.b = __shfl_sync(FULL, H.b, src);
+    Hb.e = __shfl_sync(FULL, H.e, src);
+    if ((int)lane == src) keep = false;
+    km &= ~(1u << src);
+    int rc = big_clip(c, A, Hb, first + src, P.sites, ct, counters);
+    if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW) return rc;
+    if (rc == CLIP_DONE) {
+      c.dirty = true;
+      if (counters) ct.clips++;
+    }
+  }
+  return CLIP_NONE;
+}
+
+// Volume and first moment about the vertex mean (same fan tetrahedra as the
+// register path), using the pair hash for the edge successors; cells that
+// fail the FP32 error estimate are integrated again in FP64, with the FP64
+// vertex positions kept in the arena's staging arrays.
+__device__ inline void big_volume(const BigCell& c, const BigArena& A, const float4* __restrict__ sites, double& V,
+                                  double& ox, double& oy, double& oz, Counters& ct) {
+  const uint32_t hmask = big_hash_vertices(c, A);
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = (int)lane_id(); i < c.nv; i += 32) {
+    float4 v = A.vp[i];
+    sx += v.x;
+    sy += v.y;
+    sz += v.z;
+  }
+  const float cx = warp_sumf(sx) / c.nv, cy = warp_sumf(sy) / c.nv, cz = warp_sumf(sz) / c.nv;
+  float Vf = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, Sabs = 0.f, emax = 0.f;
+  for (int it = (int)lane_id(); it < 3 * c.nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t q = bpair(A.vt[t], rho);
+    uint32_t fy = q >> 16;
+    int u = hash_find(A, brev(q), hmask);
+    if (u < 0) continue;
+    float4 pf = A.pl[fy];
+    float hgt = fmaf(pf.x, cx, fmaf(pf.y, cy, fmaf(pf.z, cz, -pf.w)));
+    float gx = -hgt * pf.x, gy = -hgt * pf.y, gz = -hgt * pf.z;
+    float4 a = A.vp[t], b = A.vp[u];
+    float ax = a.x - cx, ay = a.y - cy, az = a.z - cz;
+    float bx = b.x - cx, by = b.y - cy, bz = b.z - cz;
+    float det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
+    Vf += det;
+    Mx += det * (gx + ax + bx);
+    My += det * (gy + ay + by);
+    Mz += det * (gz + az + bz);
+    float e1x = ax - gx, e1y = ay - gy, e1z = az - gz, e2x = bx - gx, e2y = by - gy, e2z = bz - gz;
+    float crx = e1y * e2z - e1z * e2y, cry = e1z * e2x - e1x * e2z, crz = e1x * e2y - e1y * e2x;
+    Sabs += sqrtf(crx * crx + cry * cry + crz * crz);
+    emax = fmaxf(emax, a.w);
+  }
+  Vf = warp_sumf(Vf) * (1.0f / 6.0f);
+  Mx = warp_sumf(Mx) * (1.0f / 24.0f);
+  My = warp_sumf(My) * (1.0f / 24.0f);
+  Mz = warp_sumf(Mz) * (1.0f / 24.0f);
+  Sabs = warp_sumf(Sabs) * 0.5f;
+  emax = warp_maxf(emax);
+  float L = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; k++) L += fmaxf(c.alo[k] * c.alo[k], c.ahi[k] * c.ahi[k]);
+  L = sqrtf(L);
+  ox = cx;
+  oy = cy;
+  oz = cz;
+  V = Vf;
+  if (!volume_needs_fp64(Vf, L, Sabs, emax)) {
+    if (Vf > 0.f) {
+      ox += Mx / Vf;
+      oy += My / Vf;
+      oz += Mz / Vf;
+    }
+    return;
+  }
+  ct.refvol++;
+  // FP64 vertex positions: x, y in nvp (as two doubles), z in otri
+  double2* p2 = reinterpret_cast<double2*>(A.nvp);
+  double* pz = reinterpret_cast<double*>(A.otri);
+  for (int i = (int)lane_id(); i < c.nv; i += 32) {
+    uint64_t T = A.vt[i];
+    double x, y, z;
+    vertex64(bfield(T, 0), bfield(T, 1), bfield(T, 2), A.pid, c.me, c.lo, c.hi, sites, x, y, z);
+    p2[i] = make_double2(x, y);
+    pz[i] = z;
+  }
+  __syncwarp();
+  double Vd = 0.0, Mxd = 0.0, Myd = 0.0, Mzd = 0.0;
+  const double dcx = cx, dcy = cy, dcz = cz;
+  for (int it = (int)lane_id(); it < 3 * c.nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t q = bpair(A.vt[t], rho);
+    uint32_t fy = q >> 16;
+    int u = hash_find(A, brev(q), hmask);
+    if (u < 0) continue;
+    PlaneT<double> pf = plane64(A.pid[fy], c.me, c.lo, c.hi, sites);
+    double hgt = pf.nx * dcx + pf.ny * dcy + pf.nz * dcz - pf.b;
+    double gx = -hgt * pf.nx, gy = -hgt * pf.ny, gz = -hgt * pf.nz;
+    double2 a2 = p2[t], b2 = p2[u];
+    double ax = a2.x - dcx, ay = a2.y - dcy, az = pz[t] - dcz;
+    double bx = b2.x - dcx, by = b2.y - dcy, bz = pz[u] - dcz;
+    double det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
+    Vd += det;
+    Mxd += det * (gx + ax + bx);
+    Myd += det * (gy + ay + by);
+    Mzd += det * (gz + az + bz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Vd += __shfl_xor_sync(FULL, Vd, o);
+    Mxd += __shfl_xor_sync(FULL, Mxd, o);
+    Myd += __shfl_xor_sync(FULL, Myd, o);
+    Mzd += __shfl_xor_sync(FULL, Mzd, o);
+  }
+  V = Vd / 6.0;
+  if (V > 0.0) {
+    ox += Mxd / 24.0 / V;
+    oy += Myd / 24.0 / V;
+    oz += Mzd / 24.0 / V;
+  }
+  __syncwarp();
+}
+
+// Returns false if the cell overflowed even the large capacity.
+__device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, Counters& ct, long long& empties) {
+  const unsigned lane = lane_id(), lt = lanemask_lt();
+  const bool counters = P.cfg.counters != 0;
+  BigCell c;
+  c.me = P.sites[si];
+  const int orig_i = P.perm[si];
+  const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
+  const SetInfo& SI = P.sets[set];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c.lo[k] = SI.lo[k];
+    c.hi[k] = SI.hi[k];
+  }
+  big_init(c, A);
+  bool empty = false, overflow = false;
+  int cur = SI.root;
+  bool have = true;
+  const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
+  while (true) {
+    if (have) {
+      if (ref_is_leaf(cur)) {
+        int rc = big_leaf(c, A, cur, si, orig_i, P, ct);
+        if (rc == CLIP_EMPTY) {
+          empty = true;
+          break;
+        }
+        if (rc == CLIP_OVERFLOW) {
+          overflow = true;
+          break;
+        }
+        if (c.dirty) {
+          big_aabb(c, A);
+          c.dirty = false;
+        }
+        have = false;
+      } else {
+        const float4* nd = P.nodes + 4 * (size_t)cur;
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < 4) rec = __ldg(nd + lane);
+        float4 hi;
+        hi.x = __shfl_down_sync(FULL, rec.x, 1);
+        hi.y = __shfl_down_sync(FULL, rec.y, 1);
+        hi.z = __shfl_down_sync(FULL, rec.z, 1);
+        hi.w = __shfl_down_sync(FULL, rec.w, 1);
+        float lb = 0.f, key = 0.f;
+        int occ = 0;
+        bool keep = false;
+        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, c.alo, c.ahi, c.sc, c.srad, cull, lb, occ, key);
+        int myref = __float_as_int(hi.w);
+        bool k0 = __shfl_sync(FULL, keep, 0), k1 = __shfl_sync(FULL, keep, 2);
+        float key0 = __shfl_sync(FULL, key, 0), key1 = __shfl_sync(FULL, key, 2);
+        int r0 = __shfl_sync(FULL, myref, 0), r1 = __shfl_sync(FULL, myref, 2);
+        if (counters) ct.nodes += 2;
+        if (k0 && k1) {
+          bool near0 = trav == 1 ? true : key0 <= key1;
+          int fsrc = near0 ? 2 : 0;
+          float flb = __shfl_sync(FULL, lb, fsrc);
+          int focc = __shfl_sync(FULL, occ, fsrc);
+          cur = near0 ? r0 : r1;
+          if (!big_push(c, A, flb, near0 ? r1 : r0, focc)) {
+            overflow = true;
+            break;
+          }
+        } else if (k0) {
+          cur = r0;
+        } else if (k1) {
+          cur = r1;
+        } else {
+          have = false;
+        }
+      }
+      if (have) continue;
+    }
+    if (!big_pop(c, A, cull, trav, cur)) break;
+    have = true;
+  }
+  if (overflow) return false;
+  if (empty) {
+    if (lane == 0) {
+      P.counts[orig_i] = 0;
+      P.vol[orig_i] = 0.0f;
+      P.cen[3 * (size_t)orig_i] = c.me.x;
+      P.cen[3 * (size_t)orig_i + 1] = c.me.y;
+      P.cen[3 * (size_t)orig_i + 2] = c.me.z;
+    }
+    empties++;
+    return true;
+  }
+  // neighbours: site planes that carry a face, sorted, into the pool
+  big_mark_planes(c, A);
+  int* list = reinterpret_cast<int*>(A.otri);
+  int cnt = 0;
+  for (int base = 0; base < c.npl; base += 32) {
+    int p = base + (int)lane;
+    bool isn = p < c.npl && A.flag[p] != 0 && A.pid[p] >= 0;
+    uint32_t mk = __ballot_sync(FULL, isn);
+    if (isn) list[cnt + __popc(mk & lt)] = P.perm[A.pid[p]] - SI.first;
+    cnt += __popc(mk);
+  }
+  __syncwarp();
+  long long off = 0;
+  if (cnt <= P.stride) {
+    // short list: the cell's regular row
+    int* row = P.scratch + (size_t)orig_i * P.stride;
+    for (int t = (int)lane; t < cnt; t += 32) {
+      int v = list[t];
+      int rank = 0;
+      for (int u = 0; u < cnt; u++) rank += list[u] < v;
+      row[rank] = v;
+    }
+    if (lane == 0) P.counts[orig_i] = cnt;
+  } else if (lane == 0) {
+    off = atomicAdd((unsigned long long*)&P.st->pool_used, (unsigned long long)cnt);
+  }
+  off = __shfl_sync(FULL, off, 0);
+  if (cnt <= P.stride) {
+  } else if (off + cnt > P.pool_cap) {
+    if (lane == 0) {
+      P.counts[orig_i] = 0;
+      set_error(P.st, VD_ERR_CELL_OVERFLOW);
+    }
+  } else {
+    for (int t = (int)lane; t < cnt; t += 32) {
+      int v = list[t];
+      int rank = 0;
+      for (int u = 0; u < cnt; u++) rank += list[u] < v;
+      P.pool[off + rank] = v;
+    }
+    if (lane == 0) {
+      P.counts[orig_i] = cnt;
+      P.ovf_slot[orig_i] = (int)off;
+    }
+  }
+  double V, ox, oy, oz;
+  big_volume(c, A, P.sites, V, ox, oy, oz, ct);
+  if (lane == 0) {
+    P.vol[orig_i] = (float)V;
+    P.cen[3 * (size_t)orig_i] = (float)((double)c.me.x + ox);
+    P.cen[3 * (size_t)orig_i + 1] = (float)((double)c.me.y + oy);
+    P.cen[3 * (size_t)orig_i + 2] = (float)((double)c.me.z + oz);
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void big_cells_kernel(CellBuffers P) {
+  const unsigned lane = lane_id();
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const BigArena A = big_arena(P.arena, slot);
+  Counters ct = {};
+  long long empties = 0, failed = 0;
+  const int total = min(P.st->ovf_count, P.ovf_cap);
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&P.work[1], 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= total) break;
+    const int si = P.ovf_list[item];
+    if (!big_build_cell(P, A, si, ct, empties)) {
+      failed++;
+      if (lane == 0) {
+        const int orig = P.perm[si];
+        P.counts[orig] = 0;
+        P.vol[orig] = __int_as_float(0x7fc00000);
+        set_error(P.st, VD_ERR_CELL_OVERFLOW);
+      }
+    }
+  }
+  flush_counters(P, ct, lane, empties, 0, failed);
+}
+
+template <int VPL, int PCAP, int QPL>
+static cudaError_t launch_variant(const CellBuffers& c, int num_sms, cudaStream_t s) {
   int wpb = c.cfg.warps_per_block;
-  if (BIG) wpb = 4;
-  size_t smem = sizeof(WarpSmem<VPL, PCAP>) * (size_t)wpb;
-  auto kern = cells_kernel<VPL, PCAP, QPL, BIG>;
+  size_t smem = sizeof(WarpSmem<VPL, PCAP, QPL>) * (size_t)wpb;
+  auto kern = cells_kernel<VPL, PCAP, QPL>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int per_sm = c.cfg.blocks_per_sm;
-  if (per_sm <= 0 || BIG) {
+  if (per_sm <= 0) {
     int occ = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * wpb, smem);
     if (err != cudaSuccess) return err;
     per_sm = occ > 0 ? occ : 1;
   }
-  int grid = grid_override > 0 ? grid_override : num_sms * per_sm;
-  kern<<<grid, 32 * wpb, smem, s>>>(c);
+  kern<<<num_sms * per_sm, 32 * wpb, smem, s>>>(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, const std::function<void()>& between) {
   cudaError_t err;
   const vd_config& g = c.cfg;
+  const int q = g.queue_per_lane;
   if (g.verts_per_lane >= 4) {
-    err = g.queue_per_lane >= 2 ? launch_variant<4, 64, 2, false>(c, num_sms, 0, s)
-                                : launch_variant<4, 64, 1, false>(c, num_sms, 0, s);
+    err = q >= 8   ? launch_variant<4, 128, 8>(c, num_sms, s)
+          : q >= 4 ? launch_variant<4, 128, 4>(c, num_sms, s)
+          : q >= 2 ? launch_variant<4, 128, 2>(c, num_sms, s)
+                   : launch_variant<4, 128, 1>(c, num_sms, s);
   } else {
-    err = g.queue_per_lane >= 2 ? launch_variant<2, 64, 2, false>(c, num_sms, 0, s)
-                                : launch_variant<2, 64, 1, false>(c, num_sms, 0, s);
+    err = q >= 8   ? launch_variant<2, 64, 8>(c, num_sms, s)
+          : q >= 4 ? launch_variant<2, 64, 4>(c, num_sms, s)
+          : q >= 2 ? launch_variant<2, 64, 2>(c, num_sms, s)
+                   : launch_variant<2, 64, 1>(c, num_sms, s);
   }
   if (err != cudaSuccess) return err;
   between();
-  // cells that overflowed the register-resident capacity: large-capacity
-  // pass (256 vertices, 192 planes, 256 queue entries)
-  return launch_variant<8, 192, 8, true>(c, num_sms, num_sms * 2, s);
+  // cells that overflowed the register-resident capacity
+  big_cells_kernel<<<num_sms, 32 * kBigWarpsPerBlock, 0, s>>>(c);
+  return cudaGetLastError();
 }
 
 }  // namespace vd

@@ -20,7 +20,7 @@ namespace vd {
 
 constexpr float kCullPad = 1e-5f;
 
-template <int VPL, int PCAP>
+template <int VPL, int PCAP, int QPL>
 struct WarpSmem {
   float4 pl[PCAP];   // n^x, n^y, n^z, b^ (local frame)
   float pe[PCAP];    // offset error bound per plane
@@ -28,11 +28,20 @@ struct WarpSmem {
   uint32_t otri[32 * VPL];
   float4 nvp[32 * VPL];
   uint32_t nvt[32 * VPL];
+  // best-first queue, dense in [0, qn): lower bound, node reference,
+  // occupied-octant bits | push sequence << 8
+  float qlb[32 * QPL];
+  int qref[32 * QPL];
+  int qocc[32 * QPL];
 };
 
 struct Counters {
-  long long cand, clips, nodes, vtests, newv, fp64, fp64amb;
+  long long cand, clips, nodes, vtests, newv, fp64, fp64amb, refv, refvol;
 };
+
+// A new vertex whose FP32 error bound exceeds this fraction of its |x|_1
+// (nearly parallel planes) is re-solved in FP64 from the original inputs.
+constexpr float kRefineRel = 8192.0f * 5.9604644775390625e-8f;
 
 template <int VPL, int PCAP, int QPL>
 struct Cell {
@@ -41,22 +50,19 @@ struct Cell {
   // vertices (per lane)
   float vx[VPL], vy[VPL], vz[VPL], ve[VPL];
   uint32_t vt[VPL];
-  // best-first queue (per lane)
-  float qlb[QPL];
-  int qref[QPL];
-  int qocc[QPL];  // occupied-octant bits | push sequence << 8; < 0 = empty
   // warp-uniform state
   float4 me;
   float lo[3], hi[3];  // the set's box
   float alo[3], ahi[3];
+  float sc[3], srad;  // bounding sphere of the cell (local frame)
   int nv;
   uint32_t freem[NPW];
-  int seq;
+  int qn, seq;
   bool dirty;
 };
 
-template <int VPL, int PCAP>
-__device__ __forceinline__ PlaneT<float> load_plane(const WarpSmem<VPL, PCAP>& S, int k) {
+template <int VPL, int PCAP, int QPL>
+__device__ __forceinline__ PlaneT<float> load_plane(const WarpSmem<VPL, PCAP, QPL>& S, int k) {
   float4 t = S.pl[k];
   PlaneT<float> P;
   P.nx = t.x;
@@ -77,8 +83,8 @@ __device__ __forceinline__ PlaneT<double> plane64(int id, const float4& me, cons
 }
 
 // FP64 re-evaluation of "vertex tri lies outside the plane of site hpid".
-template <int VPL, int PCAP>
-__device__ __noinline__ bool resolve64(const WarpSmem<VPL, PCAP>& S, uint32_t tri, int hpid, float4 me,
+template <int VPL, int PCAP, int QPL>
+static __device__ __noinline__ bool resolve64(const WarpSmem<VPL, PCAP, QPL>& S, uint32_t tri, int hpid, float4 me,
                                        const float* lo, const float* hi, const float4* __restrict__ sites,
                                        long long& amb) {
   PlaneT<double> A = plane64(S.pid[tri & 255u], me, lo, hi, sites);
@@ -90,6 +96,23 @@ __device__ __noinline__ bool resolve64(const WarpSmem<VPL, PCAP>& S, uint32_t tr
   double s = side<double>(H, x, y, z);
   if (ambiguous<double>(s, e, H.e)) amb++;
   return s > 0.0;
+}
+
+// FP64 re-solve of the vertex of planes (pa, pb, ph) (plane ids: sorted
+// site index or -1-face); the FP32 result's bound becomes the FP64 bound plus
+// one rounding to float and the terms of a later FP32 sign test.
+static __device__ __noinline__ void refine_vertex(int pa, int pb, int ph, float4 me, const float* lo, const float* hi,
+                                           const float4* __restrict__ sites, float& x, float& y, float& z,
+                                           float& e) {
+  PlaneT<double> A = plane64(pa, me, lo, hi, sites), B = plane64(pb, me, lo, hi, sites),
+                 H = plane64(ph, me, lo, hi, sites);
+  double X, Y, Z, E;
+  vertex3<double>(A, B, H, X, Y, Z, E);
+  x = (float)X;
+  y = (float)Y;
+  z = (float)Z;
+  float x1 = fabsf(x) + fabsf(y) + fabsf(z);
+  e = (E < 1e30) ? (float)(E * (1.0 + 1e-6)) + 12.0f * Num<float>::u * x1 * 1.0001f : INFINITY;
 }
 
 // squared directional radius over the octants in `occ` (Sec. 4.2.1/4.2.2):
@@ -106,6 +129,16 @@ __device__ __forceinline__ float dir_radius2(int occ, const float* alo, const fl
     r2 += fmaxf(a, b);
   }
   return r2;
+}
+
+// Upper bound on the cell's extent toward any site in the octants `occ`:
+// the directional AABB radius, capped by the bounding sphere's reach
+// |center| + radius (valid in every direction).
+__device__ __forceinline__ float cell_radius(int occ, const float* alo, const float* ahi, const float* sc, float srad,
+                                             int cull_mode) {
+  float R = sqrtf(dir_radius2(occ, alo, ahi, cull_mode));
+  if (cull_mode == 0) R = fminf(R, sqrtf(sc[0] * sc[0] + sc[1] * sc[1] + sc[2] * sc[2]) + srad);
+  return R;
 }
 
 template <int VPL, int PCAP, int QPL>
@@ -127,104 +160,137 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c) {
   for (int k = 0; k < 3; k++) {
     c.alo[k] = warp_minf(mn[k]) - em;
     c.ahi[k] = warp_maxf(mx[k]) + em;
+    c.sc[k] = 0.5f * (c.alo[k] + c.ahi[k]);
   }
+  float r2 = 0.0f;
+#pragma unroll
+  for (int r = 0; r < VPL; r++)
+    if (c.vt[r] != kEmptyTri) {
+      float dx = c.vx[r] - c.sc[0], dy = c.vy[r] - c.sc[1], dz = c.vz[r] - c.sc[2];
+      r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+    }
+  c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
 }
 
 // Test of one BVH child box [lo.xyz, hi.xyz] with maximum weight lo.w
-// (Sec. 4.2.2): d = distance from the site to the box, lower bound of every
-// d_ij in the box LB = d/2 + min(0, w_i - w_max)/(2d); culled iff LB exceeds
-// the directional radius over the octants the box occupies. Returns keep;
-// lb is a safe (padded) LB, key the best-first key LB - R.
+// (Sec. 4.2.2). For a site j in the box at distance D in [dmin, dmax],
+// d_ij = D/2 + (w_i - w_j)/(2D) >= f(D) = D/2 + c/(2D), c = w_i - w_max.
+// f is increasing for c <= 0, so LB = f(dmin) -- the paper's bound; for
+// c > 0 it is convex with its minimum at sqrt(c), so LB = f(clamp(sqrt c,
+// dmin, dmax)) (tighter than the paper's dmin/2 for heavy sites). Culled
+// iff LB exceeds the cell radius over the octants the box occupies.
+// Returns keep; lb is a safe (padded) LB, key the best-first key LB - R.
 __device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* alo, const float* ahi,
-                                          int cull_mode, float& lb, int& occ, float& key) {
+                                          const float* sc, float srad, int cull_mode, float& lb, int& occ,
+                                          float& key) {
   float rl[3] = {lo.x - me.x, lo.y - me.y, lo.z - me.z};
   float rh[3] = {hi.x - me.x, hi.y - me.y, hi.z - me.z};
-  float d2 = 0.0f;
+  float d2 = 0.0f, f2 = 0.0f;
   occ = 0;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     float dk = fmaxf(fmaxf(rl[k], -rh[k]), 0.0f);
+    float fk = fmaxf(fabsf(rl[k]), fabsf(rh[k]));
     d2 = fmaf(dk, dk, d2);
+    f2 = fmaf(fk, fk, f2);
     occ |= (rh[k] >= 0.0f ? 1 : 0) << (2 * k);
     occ |= (rl[k] <= 0.0f ? 1 : 0) << (2 * k + 1);
   }
-  float R = sqrtf(dir_radius2(occ, alo, ahi, cull_mode));
-  if (d2 == 0.0f) {
+  float R = cell_radius(occ, alo, ahi, sc, srad, cull_mode);
+  float c = me.w - lo.w;
+  float D = sqrtf(d2);
+  if (c > 0.0f) D = fminf(fmaxf(sqrtf(c), D), sqrtf(f2) * (1.0f + kCullPad));
+  if (!(D > 0.0f)) {
     lb = -INFINITY;
     key = -R;
     return true;
   }
-  float d = sqrtf(d2);
-  float c = fminf(0.0f, me.w - lo.w);
-  lb = (d2 + c - kCullPad * (d2 + fabsf(me.w) + fabsf(lo.w))) / (2.0f * d);
-  key = (d2 + c) / (2.0f * d) - R;
+  float D2 = D * D;
+  lb = (D2 + c - kCullPad * (D2 + fabsf(me.w) + fabsf(lo.w))) / (2.0f * D);
+  key = (D2 + c) / (2.0f * D) - R;
   if (cull_mode == 2) return true;
   return !(lb > R * (1.0f + kCullPad));
 }
 
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ bool queue_push(Cell<VPL, PCAP, QPL>& c, float lb, int ref, int occ) {
-  const unsigned lane = lane_id();
-#pragma unroll
-  for (int r = 0; r < QPL; r++) {
-    unsigned fm = __ballot_sync(FULL, c.qocc[r] < 0);
-    if (fm) {
-      if (lane == (unsigned)(__ffs(fm) - 1)) {
-        c.qlb[r] = lb;
-        c.qref[r] = ref;
-        c.qocc[r] = occ | (c.seq << 8);
-      }
-      c.seq++;
-      return true;
-    }
+__device__ __forceinline__ bool queue_push(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, float lb, int ref,
+                                           int occ) {
+  if (c.qn >= 32 * QPL) return false;
+  if (lane_id() == 0) {
+    S.qlb[c.qn] = lb;
+    S.qref[c.qn] = ref;
+    S.qocc[c.qn] = occ | (c.seq << 8);
   }
-  return false;
+  c.qn++;
+  c.seq++;
+  __syncwarp();
+  return true;
 }
 
 // Pop the most promising entry still valid under the current cell bounds
 // (Alg. 1 backtracking: re-test with the shrunken radii; entries that now
-// fail are discarded). Depth-first mode pops the newest entry.
+// fail are dropped). The queue is kept unsorted and the popped slot takes
+// the last entry (App. A.5); the minimum is one redux.sync over the lanes.
+// Depth-first mode pops the newest entry.
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ bool queue_pop(Cell<VPL, PCAP, QPL>& c, int cull_mode, int traversal, int& ref) {
-  const unsigned lane = lane_id();
-  uint32_t best = 0xffffffffu;
-  int bslot = 0;
-#pragma unroll
-  for (int r = 0; r < QPL; r++) {
-    if (c.qocc[r] >= 0) {
-      float R = sqrtf(dir_radius2(c.qocc[r] & 63, c.alo, c.ahi, cull_mode));
-      if (cull_mode != 2 && c.qlb[r] > R * (1.0f + kCullPad)) {
-        c.qocc[r] = -1;
-        continue;
-      }
-      uint32_t k = traversal == 0 ? f2o(c.qlb[r] - R) : (0xfffffffeu - (uint32_t)(c.qocc[r] >> 8));
-      if (k < best) {
-        best = k;
-        bslot = r;
+__device__ __forceinline__ bool queue_pop(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int cull_mode,
+                                          int traversal, int& ref) {
+  const unsigned lane = lane_id(), lt = lanemask_lt();
+  int live = 0;
+  uint32_t bestk = 0xffffffffu;
+  int besti = 0x7fffffff;
+  for (int base = 0; base < c.qn; base += 32) {
+    int i = base + (int)lane;
+    bool ok = false;
+    float lb = 0.f;
+    int rf = 0, oc = 0;
+    uint32_t key = 0xffffffffu;
+    if (i < c.qn) {
+      lb = S.qlb[i];
+      rf = S.qref[i];
+      oc = S.qocc[i];
+      float R = cell_radius(oc & 63, c.alo, c.ahi, c.sc, c.srad, cull_mode);
+      ok = cull_mode == 2 || !(lb > R * (1.0f + kCullPad));
+      key = traversal == 0 ? f2o(lb - R) : (0xfffffffeu - (uint32_t)(oc >> 8));
+    }
+    uint32_t km = __ballot_sync(FULL, ok);
+    int dst = live + __popc(km & lt);
+    __syncwarp();
+    if (ok) {
+      S.qlb[dst] = lb;
+      S.qref[dst] = rf;
+      S.qocc[dst] = oc;
+      if (key < bestk) {
+        bestk = key;
+        besti = dst;
       }
     }
+    live += __popc(km);
+    __syncwarp();
   }
-  uint32_t mn = __reduce_min_sync(FULL, best);
-  if (mn == 0xffffffffu) return false;
-  int src = __ffs(__ballot_sync(FULL, best == mn)) - 1;
-  int mine = 0;
-#pragma unroll
-  for (int r = 0; r < QPL; r++)
-    if (r == bslot) mine = c.qref[r];
-  ref = __shfl_sync(FULL, mine, src);
-  if ((int)lane == src) {
-#pragma unroll
-    for (int r = 0; r < QPL; r++)
-      if (r == bslot) c.qocc[r] = -1;
+  c.qn = live;
+  uint32_t mn = __reduce_min_sync(FULL, bestk);
+  if (live == 0 || mn == 0xffffffffu) return false;
+  int idx = (int)__reduce_min_sync(FULL, bestk == mn ? (uint32_t)besti : 0x7fffffffu);
+  ref = S.qref[idx];
+  __syncwarp();
+  if (lane == 0) {
+    int last = c.qn - 1;
+    S.qlb[idx] = S.qlb[last];
+    S.qref[idx] = S.qref[last];
+    S.qocc[idx] = S.qocc[last];
   }
+  c.qn--;
+  __syncwarp();
   return true;
 }
 
-enum { CLIP_NONE = 0, CLIP_DONE = 1, CLIP_EMPTY = 2, CLIP_OVERFLOW = 3 };
+enum { CLIP_NONE = 0, CLIP_DONE = 1, CLIP_EMPTY = 2, CLIP_OVERFLOW = 3, CLIP_OVF_PLANES = 4 };
+enum { OVF_QUEUE = 0, OVF_VERTICES = 1, OVF_PLANES = 2, OVF_NEIGHBORS = 3 };
 
 // Clip the cell by plane H of site hpid (App. B "Clipping by a half-space").
 template <int VPL, int PCAP, int QPL>
-__device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, const PlaneT<float>& H, int hpid,
+__device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, const PlaneT<float>& H, int hpid,
                          const float4* __restrict__ sites, Counters& ct, bool counters) {
   constexpr int VCAP = Cell<VPL, PCAP, QPL>::VCAP;
   constexpr int NPW = Cell<VPL, PCAP, QPL>::NPW;
@@ -278,7 +344,7 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, const 
       c.freem[w] = ~__reduce_or_sync(FULL, lm[w]);
       if (c.freem[w]) h = 32 * w + __ffs(c.freem[w]) - 1;
     }
-    if (h < 0) return CLIP_OVERFLOW;
+    if (h < 0) return CLIP_OVF_PLANES;
   }
 #pragma unroll
   for (int w = 0; w < NPW; w++)
@@ -329,6 +395,10 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, const 
         PlaneT<float> A = load_plane(S, (int)a), B = load_plane(S, (int)b);
         float x, y, z, ev;
         vertex3<float>(A, B, H, x, y, z, ev);
+        if (!(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
+          refine_vertex(S.pid[a], S.pid[b], hpid, c.me, c.lo, c.hi, sites, x, y, z, ev);
+          ct.refv++;
+        }
         S.nvp[slot] = make_float4(x, y, z, ev);
         S.nvt[slot] = a | (b << 8) | ((uint32_t)h << 16);
       }
@@ -365,9 +435,40 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, const 
 }
 
 
+// Candidate pre-test of Sec. 4.2.1: the plane n.x <= beta can cut the cell
+// only if it cuts the cell's AABB, i.e. n.c_o > beta for the AABB corner c_o
+// of n's octant (the exact support of the box in direction n; the paper's
+// per-octant corner distance |c_o| bounds it from above).
+__device__ __forceinline__ bool candidate_test(float nx, float ny, float nz, float nn, float beta, float wi,
+                                               float wj, const float* alo, const float* ahi, const float* sc,
+                                               float srad, int cull_mode) {
+  if (cull_mode == 2) return true;
+  float n[3] = {nx, ny, nz};
+  float pad = 0.5f * (nn + fabsf(wi) + fabsf(wj));
+  if (cull_mode == 1) {
+    float R = sqrtf(dir_radius2(0, alo, ahi, 1));
+    float len = sqrtf(nn);
+    pad = kCullPad * (pad + len * R);
+    return len * R * (1.0f + kCullPad) > beta - pad;
+  }
+  float sup = 0.0f, mag = 0.0f, n1 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    float t = n[k] > 0.0f ? n[k] * ahi[k] : (n[k] < 0.0f ? n[k] * alo[k] : 0.0f);
+    sup += t;
+    mag += fabsf(t);
+    n1 += fabsf(n[k]);
+  }
+  if (!(sup > beta - kCullPad * (pad + mag))) return false;
+  // bounding sphere: n.sc + srad |n| > beta  <=>  srad^2 nn > (beta - n.sc)^2 when beta > n.sc
+  float ns = n[0] * sc[0] + n[1] * sc[1] + n[2] * sc[2];
+  float rhs = beta - ns - kCullPad * (pad + n1 * (fabsf(sc[0]) + fabsf(sc[1]) + fabsf(sc[2]) + srad));
+  return rhs <= 0.0f || srad * srad * nn > rhs * rhs;
+}
+
 // Start a cell as the box: 6 planes, 8 corners (App. B "Initialization").
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S) {
+__device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S) {
   constexpr int NPW = Cell<VPL, PCAP, QPL>::NPW;
   const unsigned lane = lane_id();
   if (lane < 6) {
@@ -395,8 +496,7 @@ __device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL,
 #pragma unroll
   for (int w = 0; w < NPW; w++) c.freem[w] = 0xffffffffu;
   c.freem[0] = ~63u;
-#pragma unroll
-  for (int r = 0; r < QPL; r++) c.qocc[r] = -1;
+  c.qn = 0;
   c.seq = 0;
   c.dirty = false;
   recompute_aabb(c);
@@ -405,7 +505,7 @@ __device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL,
 // Compact the vertices into shared memory (S.nvp / S.nvt, in slot order),
 // return their count, their coordinate sums and the planes they reference.
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ int gather_vertices(const Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP>& S, float& sx,
+__device__ __forceinline__ int gather_vertices(const Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, float& sx,
                                                float& sy, float& sz, uint32_t (&alive)[PCAP / 32]) {
   constexpr int NPW = PCAP / 32;
   const unsigned lt = lanemask_lt();
@@ -449,6 +549,73 @@ __device__ __forceinline__ int gather_vertices(const Cell<VPL, PCAP, QPL>& c, Wa
 __device__ __forceinline__ bool tri_has_pair(uint32_t T, uint32_t q) {
   uint32_t U = T | (T << 24);
   return (U & 0xffffu) == q || ((U >> 8) & 0xffffu) == q || ((U >> 16) & 0xffffu) == q;
+}
+
+// A cell's FP32 volume is accepted unless an estimate of its error says
+// otherwise: with L the largest vertex distance from the site and S the
+// summed |area| of the integration triangles, the volume error scales like
+// u L S; cells with L S > 36 V (a site far from its own cell, or a sliver)
+// or with a vertex bound above 4096 u L are integrated again in FP64.
+__device__ __forceinline__ bool volume_needs_fp64(float V, float L, float Sabs, float emax) {
+  return !(V > 0.f) || (L * Sabs > 36.f * V) || (emax > 4096.f * Num<float>::u * L);
+}
+
+__device__ __forceinline__ void vertex64(uint32_t a, uint32_t b, uint32_t c, const int* pid, float4 me, const float* lo,
+                                         const float* hi, const float4* __restrict__ sites, double& x, double& y,
+                                         double& z) {
+  double e;
+  vertex3<double>(plane64(pid[a], me, lo, hi, sites), plane64(pid[b], me, lo, hi, sites),
+                  plane64(pid[c], me, lo, hi, sites), x, y, z, e);
+}
+
+// Volume and first moment about c of the register-path polytope gathered in
+// S.nvt (slot order, nv vertices), every vertex re-solved in FP64 from the
+// original inputs: the same fan tetrahedra as the FP32 integration.
+template <int VPL, int PCAP, int QPL>
+__device__ __noinline__ void volume_fp64(const WarpSmem<VPL, PCAP, QPL>& S, int nv, float4 me, const float* lo,
+                                         const float* hi, const float4* __restrict__ sites, double cx, double cy,
+                                         double cz, double& V, double& Mx, double& My, double& Mz) {
+  V = Mx = My = Mz = 0.0;
+  for (int it = (int)lane_id(); it < 3 * nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t T = S.nvt[t];
+    uint32_t U = T | (T << 24);
+    uint32_t xy = (U >> (8 * rho)) & 0xffffu;
+    uint32_t fx = xy & 255u, fy = xy >> 8;
+    uint32_t q = fy | (fx << 8);
+    int u = 0;
+    while (u < nv && !tri_has_pair(S.nvt[u], q)) u++;
+    if (u >= nv) continue;
+    uint32_t T2 = S.nvt[u];
+    double ax, ay, az, bx, by, bz;
+    vertex64(T & 255u, (T >> 8) & 255u, (T >> 16) & 255u, S.pid, me, lo, hi, sites, ax, ay, az);
+    vertex64(T2 & 255u, (T2 >> 8) & 255u, (T2 >> 16) & 255u, S.pid, me, lo, hi, sites, bx, by, bz);
+    PlaneT<double> pf = plane64(S.pid[fy], me, lo, hi, sites);
+    double hgt = pf.nx * cx + pf.ny * cy + pf.nz * cz - pf.b;
+    double gx = -hgt * pf.nx, gy = -hgt * pf.ny, gz = -hgt * pf.nz;
+    ax -= cx;
+    ay -= cy;
+    az -= cz;
+    bx -= cx;
+    by -= cy;
+    bz -= cz;
+    double det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
+    V += det;
+    Mx += det * (gx + ax + bx);
+    My += det * (gy + ay + by);
+    Mz += det * (gz + az + bz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    V += __shfl_xor_sync(FULL, V, o);
+    Mx += __shfl_xor_sync(FULL, Mx, o);
+    My += __shfl_xor_sync(FULL, My, o);
+    Mz += __shfl_xor_sync(FULL, Mz, o);
+  }
+  V /= 6.0;
+  Mx /= 24.0;
+  My /= 24.0;
+  Mz /= 24.0;
 }
 
 }  // namespace vd

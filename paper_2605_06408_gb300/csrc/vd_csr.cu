@@ -90,10 +90,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int* __r
   if (base + kScanItems >= n && base < n) offsets[n] = (int)st->nnz;
 }
 
-// one warp per row: copy the row's neighbours from the per-cell scratch row
+// one warp per row: copy the row's neighbours from its scratch row (or the
+// large-cell pool)
 __global__ void compact_kernel(const int* __restrict__ counts, const int* __restrict__ offsets,
-                               const int* __restrict__ scratch, int stride, const int* __restrict__ scratch_big,
-                               int stride_big, const int* __restrict__ ovf_slot, int n, int* __restrict__ nbrs,
+                               const int* __restrict__ scratch, int stride, const int* __restrict__ pool,
+                               const int* __restrict__ ovf_slot, int n, int* __restrict__ nbrs,
                                long long cap, const DevStatus* st) {
   long long nnz = st->nnz;
   if (nnz > cap || nnz > 0x7fffffffLL) return;
@@ -103,7 +104,7 @@ __global__ void compact_kernel(const int* __restrict__ counts, const int* __rest
     int cnt = counts[row];
     if (cnt <= 0) continue;
     int slot = ovf_slot[row];
-    const int* src = slot >= 0 ? scratch_big + (size_t)slot * stride_big : scratch + (size_t)row * stride;
+    const int* src = slot >= 0 ? pool + slot : scratch + (size_t)row * stride;
     int* dst = nbrs + offsets[row];
     for (int k = lane; k < cnt; k += 32) dst[k] = src[k];
   }
@@ -131,8 +132,8 @@ cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbor
   if (neighbors && cap > 0) {
     int blocks = (n + 7) / 8;
     if (blocks > 65536) blocks = 65536;
-    compact_kernel<<<blocks, 256, 0, s>>>(c.counts, offsets, c.scratch, c.stride, c.scratch_big, c.stride_big,
-                                          c.ovf_slot, n, neighbors, neighbors ? cap : 0, c.st);
+    compact_kernel<<<blocks, 256, 0, s>>>(c.counts, offsets, c.scratch, c.stride, c.pool, c.ovf_slot, n,
+                                          neighbors, neighbors ? cap : 0, c.st);
   }
   finish_status_kernel<<<1, 1, 0, s>>>(c.st, neighbors ? cap : 0x7fffffffffffffffLL, nnz_out, user_status);
   return cudaGetLastError();

@@ -21,6 +21,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kMaxLeaf = 32;            // leaf sizes 1..32 (one site per lane)
 constexpr int kMaxSites = 1 << 26;      // leaf refs pack the first site in 26 bits
 constexpr int kMaxSets = 1024;
+constexpr int kBigWarpsPerBlock = 8;  // large-cell path: one block of this many warps per SM
 constexpr uint32_t kEmptyTri = 0xffffffffu;
 
 // Leaf references: bit 31 set, bits 26..30 = count-1, bits 0..25 = first.
@@ -46,6 +47,10 @@ struct DevStatus {
   long long nodes;
   long long vertex_tests;
   long long new_vertices;
+  long long pool_used;  // ints of the large-cell neighbour pool in use
+  long long refined_vertices;
+  long long refined_volumes;
+  long long ovf_reason[4];  // queue, vertices, planes, neighbours
 };
 
 __device__ inline void set_error(DevStatus* st, int code) { atomicCAS(&st->error, 0, code); }
@@ -76,25 +81,49 @@ struct PlaneT {
   T nx, ny, nz, b, e;
 };
 
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct):
+// a + b = s + err and a * a = p + err exactly in floating point.
+template <typename T>
+__device__ __forceinline__ T two_sum_err(T a, T b, T s) {
+  T bb = s - a;
+  return (a - (s - bb)) + (b - bb);
+}
+
 // Radical plane of site q (weight wj) in the frame of site p (weight wi):
 // n.x~ <= (|n|^2 + wi - wj)/2 with n = q - p (Eq. 1), normalised so that b
-// is the power distance d_ij of Eq. 2. Error bound derivation: n_k carries
-// one rounding, |n|^2 at most 5.1u relative, b = (|n|^2 + (wi-wj))/2 at most
-// 3.1u (|n|^2+|wi|+|wj|), 1/|n| at most 4.6u and each product one more u;
-// 9u|b| also covers the rounding of one fused sign test.
+// is the power distance d_ij of Eq. 2. The offset is formed in compensated
+// (float-float) arithmetic: each n_k = s_k + e_k exactly, s_k^2 = h_k + l_k
+// exactly, the large terms are summed with TwoSum and the small ones added
+// once, so 2b = |n|^2 + wi - wj carries a single rounding (u |2b|) plus
+// terms of order u^2 (|n|^2 + |wi| + |wj|). With 1/|n| and the normal good
+// to a few u, |b - b_exact| <= 6u|b| + 64u^2 (|n|^2 + |wi| + |wj|)/|n|;
+// 10u|b| covers that and the 3u|b| of one fused sign test, so the bound
+// scales with the plane's distance from p, not with |q - p|.
 template <typename T>
 __device__ __forceinline__ PlaneT<T> site_plane(T px, T py, T pz, T wi, T qx, T qy, T qz, T wj) {
   const T u = Num<T>::u;
-  T nx = qx - px, ny = qy - py, nz = qz - pz;
-  T nn = fma(nx, nx, fma(ny, ny, nz * nz));
+  T sx = qx - px, sy = qy - py, sz = qz - pz;
+  T ex = two_sum_err(qx, -px, sx), ey = two_sum_err(qy, -py, sy), ez = two_sum_err(qz, -pz, sz);
+  T hx = sx * sx, hy = sy * sy, hz = sz * sz;
+  T small = fma(sx, sx, -hx) + fma(sy, sy, -hy) + fma(sz, sz, -hz);
+  small += fma(T(2) * sx, ex, ex * ex) + fma(T(2) * sy, ey, ey * ey) + fma(T(2) * sz, ez, ez * ez);
+  T h1 = hx + hy;
+  T c = two_sum_err(hx, hy, h1);
+  T h2 = h1 + hz;
+  c += two_sum_err(h1, hz, h2);
+  T d = wi - wj;
+  T cd = two_sum_err(wi, -wj, d);
+  T A = h2 + d;
+  T ca = two_sum_err(h2, d, A);
+  T twob = A + (((ca + c) + small) + cd);
+  T nn = h2 + (c + small);
   T r = T(1) / sqrt(nn);
-  T b = T(0.5) * (nn + (wi - wj));
   PlaneT<T> P;
-  P.nx = nx * r;
-  P.ny = ny * r;
-  P.nz = nz * r;
-  P.b = b * r;
-  P.e = T(4) * u * (nn + fabs(wi) + fabs(wj)) * r + T(9) * u * fabs(P.b);
+  P.nx = fma(ex, r, sx * r);
+  P.ny = fma(ey, r, sy * r);
+  P.nz = fma(ez, r, sz * r);
+  P.b = T(0.5) * twob * r;
+  P.e = T(10) * u * fabs(P.b) + T(64) * u * u * (nn + fabs(wi) + fabs(wj)) * r;
   return P;
 }
 
@@ -200,6 +229,7 @@ struct BvhBuffers {
 
 struct CellBuffers {
   const float4* sites;   // sorted packed sites
+  const unsigned char* loser;  // sorted index: an exact duplicate site beats it
   const int* perm;       // sorted -> original index
   const float4* nodes;
   const uint64_t* keys;  // sorted keys (set id in the top bits)
@@ -210,11 +240,12 @@ struct CellBuffers {
   int* counts;           // [n] by original index
   int* scratch;          // [n * stride]
   int stride;
-  int* scratch_big;      // [ovf_cap * stride_big]
-  int stride_big;
+  int* pool;             // neighbour lists of large cells
+  long long pool_cap;
+  char* arena;           // per-warp arenas of the large-cell path
   int* ovf_list;         // [ovf_cap] sorted indices of overflowed cells
   int ovf_cap;
-  int* ovf_slot;         // [n] by original index: row in scratch_big or -1
+  int* ovf_slot;         // [n] by original index: offset in `pool` or -1
   float* vol;
   float* cen;
   int* work;             // [2] work counters (main pass, overflow pass)
@@ -238,8 +269,10 @@ struct BackBuffers {
   int* work;            // [2]
 };
 
-cudaError_t launch_pack_keys(const float* xyz, const float* w, int n, const SetInfo* sets, int nsets,
-                             const int* unused, int set_shift, uint64_t* keys, int* vals, DevStatus* st,
+cudaError_t launch_weight_range(const float* w, int n, const SetInfo* sets, int nsets, unsigned* wr,
+                                cudaStream_t s);
+cudaError_t launch_pack_keys(const float* xyz, const float* w, int n, const SetInfo* sets, int nsets, int set_shift,
+                             int bin_shift, const unsigned* wr, uint64_t* keys, int* vals, DevStatus* st,
                              cudaStream_t s);
 cudaError_t radix_sort_pairs(uint64_t*& keys, uint64_t*& keys_alt, int*& vals, int*& vals_alt, unsigned* hist,
                              int n, int bits, cudaStream_t s);
@@ -252,5 +285,7 @@ cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbor
                        long long* block_sums, int32_t* user_status, bool recount, cudaStream_t s);
 cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s);
 cudaError_t launch_inverse_perm(const int* perm, int n, int* inv, cudaStream_t s);
+cudaError_t launch_mark_losers(const uint64_t* keys, const float4* sites, const int* perm, int n,
+                               unsigned char* loser, cudaStream_t s);
 
 }  // namespace vd

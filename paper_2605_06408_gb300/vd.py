@@ -71,8 +71,9 @@ class VdStatus(ctypes.Structure):
     _fields_ = [("error", ctypes.c_int32), ("reserved", ctypes.c_int32)] + [
         (k, ctypes.c_int64)
         for k in ("nnz", "empty_cells", "overflow_cells", "failed_cells", "fp64_fallbacks", "fp64_ambiguous",
-                  "candidates", "clips", "nodes", "vertex_tests", "new_vertices")
-    ]
+                  "candidates", "clips", "nodes", "vertex_tests", "new_vertices", "refined_vertices",
+                  "refined_volumes")
+    ] + [("overflow_reason", ctypes.c_int64 * 4)]
 
 
 _lock = threading.Lock()
@@ -320,7 +321,9 @@ class Context:
     def status(self) -> dict:
         st = VdStatus()
         _check(self._lib.vd_get_status(self._h, ctypes.byref(st)), "vd_get_status")
-        return {k: getattr(st, k) for k, _ in VdStatus._fields_ if k != "reserved"}
+        d = {k: getattr(st, k) for k, _ in VdStatus._fields_ if k not in ("reserved", "overflow_reason")}
+        d["overflow_reason"] = dict(zip(("queue", "vertices", "planes", "neighbors"), list(st.overflow_reason)))
+        return d
 
 
 class _CellsFn(torch.autograd.Function):

@@ -139,6 +139,9 @@ def test_duplicates_and_outside_sites():
     r = oracle.cells(x)
     assert r["vol"][2] == 0.0 and r["counts"][2] == 0  # equal weight: lower index wins
     assert r["vol"][0] > 0
+    assert np.all(np.isfinite(r["vol"])) and r["vol"].sum() == pytest.approx(1.0, rel=1e-12)
+    assert all(2 not in nb for nb in r["nbrs"])  # the loser is nobody's neighbour
+    assert r["stats"]["ambiguous"] == 0
     w = np.array([0.0, 0.0, 0.01, 0.0], np.float32)
     r = oracle.cells(x, w)
     assert r["vol"][0] == 0.0 and r["vol"][2] > 0  # larger weight wins
