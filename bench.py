@@ -39,6 +39,8 @@ WORKLOADS = {
                  "[1e-3,1e-1]) + 10% uniform background, unit box, float32, seed 1",
     "power1M": "power diagram of the mixture1M sites with w = r^2, r = 0.2 nn exp(N(0,1)), seed 2",
     "uniform10k": "Voronoi of 10,000 uniform sites in the unit cube, seed 0",
+    "mixture200k": "Voronoi of 200,000 sites of the mixture1M distribution (seed 1); the small case used for "
+                   "full ncu captures",
     "surfaces20M": "Voronoi of 20,000,000 sites in nested Gaussian shells (sigma 1e-2..1e-5) around 32 "
                    "random surfaces + 1% background, seed 4",
 }
@@ -83,6 +85,8 @@ def make_workload(name: str, rank: int):
         return x, W.power_weights(x, 2 + seed_shift), W.UNIT_BOX
     if name == "uniform10k":
         return W.uniform(10_000, 0 + seed_shift), None, W.UNIT_BOX
+    if name == "mixture200k":
+        return W.mixture(200_000, 1 + seed_shift), None, W.UNIT_BOX
     if name == "surfaces20M":
         return W.surfaces(20_000_000, 4 + seed_shift), None, W.UNIT_BOX
     raise KeyError(name)
