@@ -215,6 +215,41 @@ int vd_get_status(vd_ctx* ctx, vd_status* st);
 /* Static string for a VD_* code (never NULL). */
 const char* vd_error_string(int code);
 
+/* ------------------------------------------------- allocation-free variant */
+
+/* Limits of vd_cells_noalloc. */
+#define VD_NOALLOC_MAX_SITES 16384 /* sites per call                          */
+#define VD_NOALLOC_ROW 64          /* neighbour slots per cell in `neighbors` */
+
+/* Cells of one small point set without allocating any device memory. There
+ * is no counterpart in the paper, whose pipeline allocates its buffers; this
+ * exists for callers that cannot call cudaMalloc (code running under another
+ * framework's allocator or memory pool, loops that forbid allocation after
+ * start-up, callers that must not create a context workspace).
+ *
+ * Same cells as vd_build (Eq. 1 clipped to bbox; every other site is a
+ * candidate, culled by the same bounds), written into caller buffers:
+ *   sites_xyz : DEVICE float32 [3n];  weights : DEVICE float32 [n] or NULL.
+ *   n         : 1 <= n <= VD_NOALLOC_MAX_SITES, else VD_ERR_TOO_LARGE.
+ *   counts    : DEVICE int32 [n]: neighbour count of each cell (-1 when the
+ *               cell exceeded the register capacity or VD_NOALLOC_ROW).
+ *   neighbors : DEVICE int32 [n * VD_NOALLOC_ROW]: row i holds counts[i]
+ *               ascending neighbour indices (the rest is left unwritten).
+ *   volume    : DEVICE float32 [n];  centroid : DEVICE float32 [3n].
+ *   status    : DEVICE int32 scalar: VD_OK, VD_ERR_INVALID_ARG (non-finite
+ *               input) or VD_ERR_CELL_OVERFLOW.
+ * Scratch: a fixed file-scope device array (about 272 KB) that every GPU
+ * loading the library holds until exit. Its device address is looked up on
+ * the first call on each device (with that device current), so make that
+ * first call before any stream capture. All calls share the array and it
+ * keeps the last call's contents (the work counter and error word are
+ * cleared on every call): calls that overlap on the GPU (different streams
+ * or devices' threads racing on one device) race on it and must be
+ * serialised by the caller. Returns VD_OK / VD_ERR_INVALID_ARG /
+ * VD_ERR_TOO_LARGE / VD_ERR_CUDA. */
+int vd_cells_noalloc(const float* sites_xyz, const float* weights, int64_t n, vd_box bbox, int32_t* counts,
+                     int32_t* neighbors, float* volume, float* centroid, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ VD_ERR_TOO_LARGE = -6
 ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
     "vd_build", "vd_copy_neighbors", "vd_build_batched", "vd_backward", "vd_get_timings", "vd_get_status",
-    "vd_error_string",
+    "vd_error_string", "vd_cells_noalloc",
 )
 
 
@@ -110,6 +110,7 @@ def load_library(build_if_missing: bool = True):
         lib.vd_backward.argtypes = [P, P, P, P, P, I, P]
         lib.vd_get_status.argtypes = [P, ctypes.POINTER(VdStatus)]
         lib.vd_get_timings.argtypes = [P, ctypes.POINTER(VdTimings)]
+        lib.vd_cells_noalloc.argtypes = [P, P, I64, VdBox, P, P, P, P, P, P]
         lib.vd_error_string.argtypes = [I]
         lib.vd_error_string.restype = ctypes.c_char_p
         for f in ABI_FUNCTIONS:
