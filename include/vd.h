@@ -85,10 +85,13 @@ typedef struct {
   int32_t cull_mode;       /* 0 directional (Sec. 4.2.1), 1 isotropic (single       */
                            /*   radius, ablation), 2 none (every site is clipped)   */
   int32_t traversal;       /* 0 best-first (Alg. 1), 1 depth-first (ablation)        */
-  int32_t warps_per_block; /* persistent kernel block size in warps (1..16)          */
+  int32_t warps_per_block; /* persistent kernel block size in warps (1..8)           */
   int32_t blocks_per_sm;   /* persistent kernel grid = SMs * this (0 = occupancy)    */
   int32_t counters;        /* 1: count tests, clips and nodes (small overhead)       */
   int32_t timing;          /* 1: record CUDA events around each phase (vd_get_timings)*/
+  int32_t warm_start;      /* 1: clip each cell first with its 32 Morton-order       */
+                           /*    neighbours (App. A.6 warm start, without KNN);     */
+                           /*    default 0 (best-first reaches that leaf first)     */
 } vd_config;
 
 /* Device-side results of the last call, read back by vd_get_status. */

@@ -113,9 +113,10 @@ static int check_config(const vd_config* c) {
     return VD_ERR_INVALID_ARG;
   if (c->cull_mode < 0 || c->cull_mode > 2) return VD_ERR_INVALID_ARG;
   if (c->traversal < 0 || c->traversal > 1) return VD_ERR_INVALID_ARG;
-  if (c->warps_per_block < 1 || c->warps_per_block > 16) return VD_ERR_INVALID_ARG;
+  if (c->warps_per_block < 1 || c->warps_per_block > 8) return VD_ERR_INVALID_ARG;
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64) return VD_ERR_INVALID_ARG;
   if (c->counters < 0 || c->counters > 1 || c->timing < 0 || c->timing > 1) return VD_ERR_INVALID_ARG;
+  if (c->warm_start < 0 || c->warm_start > 1) return VD_ERR_INVALID_ARG;
   return VD_OK;
 }
 
@@ -351,6 +352,7 @@ int vd_default_config(vd_config* cfg) {
   cfg->blocks_per_sm = 0;
   cfg->counters = 0;
   cfg->timing = 0;
+  cfg->warm_start = 0;
   return VD_OK;
 }
 

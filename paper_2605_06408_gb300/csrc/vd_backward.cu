@@ -83,7 +83,7 @@ __device__ __forceinline__ void face_accumulate(float* A, const float* g, const 
 }
 
 template <int VPL, int PCAP, int QPL>
-__device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si, Counters& ct) {
+__device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si) {
   using C = Cell<VPL, PCAP, QPL>;
   constexpr int NPW = C::NPW;
   const CellBuffers& P = B.c;
@@ -94,14 +94,10 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
   const int orig_i = P.perm[si];
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    c.lo[k] = SI.lo[k];
-    c.hi[k] = SI.hi[k];
-  }
+  c.box = SI.lo;
   const int cnt = P.counts[orig_i];
   if (cnt <= 0) return true;  // empty cell (or no site faces): no moving face
-  init_cell(c, S);
+  init_cell(c, S, 0);
   const int slot = P.ovf_slot[orig_i];
   if (slot >= 0) return false;  // a long neighbour list: the large-cell adjoint
   const int* row = P.scratch + (size_t)orig_i * P.stride;
@@ -132,8 +128,8 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si,
       int hj = __shfl_sync(FULL, j, src);
       if ((int)lane == src) keep = false;
       km &= ~(1u << src);
-      int rc = clip_cell(c, S, Hb, hj, P.sites, ct, false);
-      if (rc == CLIP_OVERFLOW) return false;
+      int rc = clip_cell(c, S, Hb, hj, P.sites, false);
+      if (rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) return false;
       if (rc == CLIP_EMPTY) return true;
     }
   }
@@ -230,13 +226,14 @@ __global__ void back_kernel(BackBuffers B) {
   BackSmem<VPL, PCAP>* Sw = reinterpret_cast<BackSmem<VPL, PCAP>*>(smem_raw);
   BackSmem<VPL, PCAP>& S = Sw[threadIdx.x >> 5];
   const unsigned lane = lane_id();
-  Counters ct = {};
+  if (lane == 0) S.w.ct = WarpCounters{};
+  __syncwarp();
   while (true) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&B.work[0], 1);
     item = __shfl_sync(FULL, item, 0);
     if (item >= B.c.n) break;
-    if (!back_cell<VPL, PCAP, QPL>(B, S, item, ct) && lane == 0) {
+    if (!back_cell<VPL, PCAP, QPL>(B, S, item) && lane == 0) {
       int k = atomicAdd(B.list_count, 1);
       if (k < B.list_cap)
         B.list[k] = item;
@@ -244,7 +241,11 @@ __global__ void back_kernel(BackBuffers B) {
         set_error(B.c.st, VD_ERR_CELL_OVERFLOW);
     }
   }
-  flush_back(B, ct, lane);
+  __syncwarp();
+  if (lane == 0) {
+    if (S.w.ct.fp64) atomicAdd((unsigned long long*)&B.c.st->fp64_fallbacks, (unsigned long long)S.w.ct.fp64);
+    if (S.w.ct.fp64amb) atomicAdd((unsigned long long*)&B.c.st->fp64_ambiguous, (unsigned long long)S.w.ct.fp64amb);
+  }
 }
 
 // ---------------------------------------------------------------- large cells
@@ -264,7 +265,7 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
   }
   const int cnt = P.counts[orig_i];
   if (cnt <= 0) return true;
-  big_init(c, A);
+  big_init(c, A, 0);
   const int slot = P.ovf_slot[orig_i];
   const int* row = slot >= 0 ? P.pool + slot : P.scratch + (size_t)orig_i * P.stride;
   for (int c0 = 0; c0 < cnt; c0 += 32) {

@@ -39,10 +39,11 @@ struct BigArena {
   uint32_t* hkey;
   int* hval;
   float* acc;
+  float* rtab;  // [64] cell radius per occupied-octant mask
 };
 
 __host__ __device__ inline size_t big_arena_bytes() {
-  size_t b = 0;
+  size_t b = 64 * 4;
   b += (size_t)kBigP * (16 + 4 + 4 + 4);
   b += (size_t)kBigV * (16 + 8 + 8 + 16 + 8);
   b += (size_t)kBigQ * 12;
@@ -83,6 +84,8 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   A.hval = (int*)p;
   p += (size_t)kBigH * 4;
   A.acc = (float*)p;
+  p += (size_t)kBigP * 10 * 4;
+  A.rtab = (float*)p;
   return A;
 }
 
@@ -160,7 +163,7 @@ __device__ __forceinline__ PlaneT<float> big_plane(const BigArena& A, int k) {
   return P;
 }
 
-__device__ inline void big_aabb(BigCell& c, const BigArena& A) {
+__device__ inline void big_aabb(BigCell& c, const BigArena& A, int cull_mode) {
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, em = 0.0f;
   for (int i = (int)lane_id(); i < c.nv; i += 32) {
     float4 v = A.vp[i];
@@ -186,9 +189,10 @@ __device__ inline void big_aabb(BigCell& c, const BigArena& A) {
     r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
   }
   c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
+  fill_rtab(A.rtab, c.alo, c.ahi, c.sc, c.srad, cull_mode);
 }
 
-__device__ inline void big_init(BigCell& c, const BigArena& A) {
+__device__ inline void big_init(BigCell& c, const BigArena& A, int cull_mode) {
   const unsigned lane = lane_id();
   if (lane < 6) {
     PlaneT<float> B = box_plane<float>((int)lane, c.me.x, c.me.y, c.me.z, c.lo, c.hi);
@@ -216,7 +220,7 @@ __device__ inline void big_init(BigCell& c, const BigArena& A) {
   c.seq = 0;
   c.dirty = false;
   __syncwarp();
-  big_aabb(c, A);
+  big_aabb(c, A, cull_mode);
 }
 
 // Mark the planes referenced by the vertices in A.flag (1 / 0).
@@ -454,7 +458,7 @@ __device__ inline bool big_pop(BigCell& c, const BigArena& A, int cull_mode, int
       lb = A.qlb[i];
       rf = A.qref[i];
       oc = A.qocc[i];
-      float R = cell_radius(oc & 63, c.alo, c.ahi, c.sc, c.srad, cull_mode);
+      float R = A.rtab[oc & 63];
       ok = cull_mode == 2 || !(lb > R * (1.0f + kCullPad));
       key = traversal == 0 ? f2o(lb - R) : (0xfffffffeu - (uint32_t)(oc >> 8));
     }

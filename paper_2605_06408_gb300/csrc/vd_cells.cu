@@ -29,12 +29,13 @@ namespace vd {
 // clip with the survivors in ascending power distance d_ij (Eq. 2).
 template <int VPL, int PCAP, int QPL>
 __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int ref, int si, int orig_i,
-                            const CellBuffers& P, Counters& ct) {
+                            const CellBuffers& P, int skip0, int skip1) {
   const unsigned lane = lane_id();
   const bool counters = P.cfg.counters != 0;
   int first = leaf_first(ref), cnt = leaf_count(ref);
   int j = first + (int)lane;
-  bool act = (int)lane < cnt && j != si;
+  // sites of the warm-start window [skip0, skip1) were clipped already
+  bool act = (int)lane < cnt && j != si && (j < skip0 || j >= skip1);
   if (act) act = P.loser[j] == 0;
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) q = P.sites[j];
@@ -61,7 +62,7 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
     if (__any_sync(FULL, beats)) return CLIP_EMPTY;
   }
   uint32_t km = __ballot_sync(FULL, keep);
-  if (counters) ct.cand += __popc(km);
+  if (counters && lane == 0) S.ct.cand += __popc(km);
   while (km) {
     uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
     uint32_t mn = __reduce_min_sync(FULL, key);
@@ -74,11 +75,11 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
     Hb.e = __shfl_sync(FULL, H.e, src);
     if ((int)lane == src) keep = false;
     km &= ~(1u << src);
-    int rc = clip_cell(c, S, Hb, first + src, P.sites, ct, counters);
+    int rc = clip_cell(c, S, Hb, first + src, P.sites, counters);
     if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) return rc;
     if (rc == CLIP_DONE) {
       c.dirty = true;
-      if (counters) ct.clips++;
+      if (counters && lane == 0) S.ct.clips++;
     }
   }
   return CLIP_NONE;
@@ -86,8 +87,8 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
 
 // Build one cell and write its outputs. Returns false on overflow.
 template <int VPL, int PCAP, int QPL>
-__device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, int si, int* row, Counters& ct,
-                           long long& empties, int& reason) {
+__device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, int si, int* row, long long& empties,
+                           int& reason) {
   using C = Cell<VPL, PCAP, QPL>;
   constexpr int NPW = C::NPW;
   const unsigned lane = lane_id(), lt = lanemask_lt();
@@ -108,22 +109,37 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   }
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    c.lo[k] = SI.lo[k];
-    c.hi[k] = SI.hi[k];
+  c.box = SI.lo;
+  const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
+  init_cell(c, S, cull);
+  bool empty = false, overflow = false;
+
+  // ---- warm start (App. A.6, with the 32 Morton-order neighbours of the
+  // site instead of a KNN query: one coalesced load, no extra pass)
+  int skip0 = 0, skip1 = 0;
+  if (P.cfg.warm_start) {
+    const int lo = SI.first, hi = SI.first + SI.count;
+    skip0 = max(lo, min(si - 16, hi - 32));
+    skip1 = min(hi, skip0 + 32);
+    int rc = process_leaf(c, S, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, 0, 0);
+    if (rc == CLIP_EMPTY) empty = true;
+    if (rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) {
+      reason = rc == CLIP_OVERFLOW ? OVF_VERTICES : OVF_PLANES;
+      return false;
+    }
+    if (c.dirty) {
+      recompute_aabb(c, S, cull);
+      c.dirty = false;
+    }
   }
-  init_cell(c, S);
 
   // ---- best-first traversal (Alg. 1)
-  bool empty = false, overflow = false;
   int cur = SI.root;
-  bool have = true;
-  const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
-  while (true) {
+  bool have = !empty;
+  while (!empty) {
     if (have) {
       if (ref_is_leaf(cur)) {
-        int rc = process_leaf(c, S, cur, si, orig_i, P, ct);
+        int rc = process_leaf(c, S, cur, si, orig_i, P, skip0, skip1);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -134,7 +150,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
           break;
         }
         if (c.dirty) {
-          recompute_aabb(c);
+          recompute_aabb(c, S, cull);
           c.dirty = false;
         }
         have = false;
@@ -150,12 +166,12 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
         float lb = 0.f, key = 0.f;
         int occ = 0;
         bool keep = false;
-        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, c.alo, c.ahi, c.sc, c.srad, cull, lb, occ, key);
+        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, S.rtab, cull, lb, occ, key);
         int myref = __float_as_int(hi.w);
         bool k0 = __shfl_sync(FULL, keep, 0), k1 = __shfl_sync(FULL, keep, 2);
         float key0 = __shfl_sync(FULL, key, 0), key1 = __shfl_sync(FULL, key, 2);
         int r0 = __shfl_sync(FULL, myref, 0), r1 = __shfl_sync(FULL, myref, 2);
-        if (counters) ct.nodes += 2;
+        if (counters && lane == 0) S.ct.nodes += 2;
         if (k0 && k1) {
           bool near0 = trav == 1 ? true : key0 <= key1;
           int fsrc = near0 ? 2 : 0;
@@ -267,13 +283,13 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   double Vd = V;
   if (volume_needs_fp64(V, L, Sabs, emax)) {
     double Mxd, Myd, Mzd;
-    volume_fp64(S, nv, c.me, c.lo, c.hi, P.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
+    volume_fp64(S, nv, c.me, c.box, c.box + 3, P.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
     if (Vd > 0.0) {
       ox += Mxd / Vd;
       oy += Myd / Vd;
       oz += Mzd / Vd;
     }
-    ct.refvol++;
+    if (lane == 0) S.ct.refvol++;
   } else if (V > 0.0f) {
     ox += Mx / V;
     oy += My / V;
@@ -320,13 +336,44 @@ __device__ inline void flush_counters(const CellBuffers& P, const Counters& ct, 
   }
 }
 
+__device__ inline void flush_warp_counters(const CellBuffers& P, const WarpCounters& w, unsigned lane,
+                                           long long empties, long long overflows) {
+  if (lane != 0) return;
+  if (empties) atomicAdd((unsigned long long*)&P.st->empty_cells, (unsigned long long)empties);
+  if (overflows) atomicAdd((unsigned long long*)&P.st->overflow_cells, (unsigned long long)overflows);
+  if (w.fp64) atomicAdd((unsigned long long*)&P.st->fp64_fallbacks, (unsigned long long)w.fp64);
+  if (w.fp64amb) atomicAdd((unsigned long long*)&P.st->fp64_ambiguous, (unsigned long long)w.fp64amb);
+  if (w.refv) atomicAdd((unsigned long long*)&P.st->refined_vertices, (unsigned long long)w.refv);
+  if (w.refvol) atomicAdd((unsigned long long*)&P.st->refined_volumes, (unsigned long long)w.refvol);
+  if (P.cfg.counters) {
+    atomicAdd((unsigned long long*)&P.st->candidates, w.cand);
+    atomicAdd((unsigned long long*)&P.st->clips, w.clips);
+    atomicAdd((unsigned long long*)&P.st->nodes, w.nodes);
+    atomicAdd((unsigned long long*)&P.st->vertex_tests, w.vtests);
+    atomicAdd((unsigned long long*)&P.st->new_vertices, w.newv);
+  }
+}
+
+// VD_CELLS_MIN_BLOCKS (build option): minimum resident 256-thread blocks per
+// SM the compiler must allow for, i.e. a register cap. 2 (128 registers)
+// measured fastest on GB300 (mixture1M: 65.7 ms vs 74.4 ms uncapped, 93 ms
+// at 3 blocks / 85 registers, which spills); 0 removes the cap.
+#ifndef VD_CELLS_MIN_BLOCKS
+#define VD_CELLS_MIN_BLOCKS 2
+#endif
+#if VD_CELLS_MIN_BLOCKS > 0
+#define VD_CELLS_BOUNDS __launch_bounds__(256, VD_CELLS_MIN_BLOCKS)
+#else
+#define VD_CELLS_BOUNDS
+#endif
 template <int VPL, int PCAP, int QPL>
-__global__ void cells_kernel(CellBuffers P) {
+__global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<VPL, PCAP, QPL>* Sw = reinterpret_cast<WarpSmem<VPL, PCAP, QPL>*>(smem_raw);
   WarpSmem<VPL, PCAP, QPL>& S = Sw[threadIdx.x >> 5];
   const unsigned lane = lane_id();
-  Counters ct = {};
+  if (lane == 0) S.ct = WarpCounters{};
+  __syncwarp();
   long long empties = 0, overflows = 0;
   while (true) {
     int item = 0;
@@ -337,7 +384,7 @@ __global__ void cells_kernel(CellBuffers P) {
     const int orig = P.perm[si];
     int* row = P.scratch + (size_t)orig * P.stride;
     int reason = 0;
-    if (!build_cell<VPL, PCAP, QPL>(P, S, si, row, ct, empties, reason)) {
+    if (!build_cell<VPL, PCAP, QPL>(P, S, si, row, empties, reason)) {
       overflows++;
       if (lane == 0) atomicAdd((unsigned long long*)&P.st->ovf_reason[reason], 1ull);
       if (lane == 0) {
@@ -352,18 +399,19 @@ __global__ void cells_kernel(CellBuffers P) {
       }
     }
   }
-  flush_counters(P, ct, lane, empties, overflows, 0);
+  __syncwarp();
+  flush_warp_counters(P, S.ct, lane, empties, overflows);
 }
 
 // ---------------------------------------------------------------- large cells
 
 __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig_i, const CellBuffers& P,
-                        Counters& ct) {
+                        Counters& ct, int skip0, int skip1) {
   const unsigned lane = lane_id();
   const bool counters = P.cfg.counters != 0;
   int first = leaf_first(ref), cnt = leaf_count(ref);
   int j = first + (int)lane;
-  bool act = (int)lane < cnt && j != si;
+  bool act = (int)lane < cnt && j != si && (j < skip0 || j >= skip1);
   if (act) act = P.loser[j] == 0;
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) q = P.sites[j];
@@ -534,15 +582,28 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     c.lo[k] = SI.lo[k];
     c.hi[k] = SI.hi[k];
   }
-  big_init(c, A);
-  bool empty = false, overflow = false;
-  int cur = SI.root;
-  bool have = true;
   const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
-  while (true) {
+  big_init(c, A, cull);
+  bool empty = false, overflow = false;
+  int skip0 = 0, skip1 = 0;
+  if (P.cfg.warm_start) {
+    const int lo = SI.first, hi = SI.first + SI.count;
+    skip0 = max(lo, min(si - 16, hi - 32));
+    skip1 = min(hi, skip0 + 32);
+    int rc = big_leaf(c, A, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, ct, 0, 0);
+    if (rc == CLIP_EMPTY) empty = true;
+    if (rc == CLIP_OVERFLOW) return false;
+    if (c.dirty) {
+      big_aabb(c, A, cull);
+      c.dirty = false;
+    }
+  }
+  int cur = SI.root;
+  bool have = !empty;
+  while (!empty) {
     if (have) {
       if (ref_is_leaf(cur)) {
-        int rc = big_leaf(c, A, cur, si, orig_i, P, ct);
+        int rc = big_leaf(c, A, cur, si, orig_i, P, ct, skip0, skip1);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -552,7 +613,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
           break;
         }
         if (c.dirty) {
-          big_aabb(c, A);
+          big_aabb(c, A, cull);
           c.dirty = false;
         }
         have = false;
@@ -568,7 +629,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
         float lb = 0.f, key = 0.f;
         int occ = 0;
         bool keep = false;
-        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, c.alo, c.ahi, c.sc, c.srad, cull, lb, occ, key);
+        if (lane == 0 || lane == 2) keep = node_test(rec, hi, c.me, A.rtab, cull, lb, occ, key);
         int myref = __float_as_int(hi.w);
         bool k0 = __shfl_sync(FULL, keep, 0), k1 = __shfl_sync(FULL, keep, 2);
         float key0 = __shfl_sync(FULL, key, 0), key1 = __shfl_sync(FULL, key, 2);

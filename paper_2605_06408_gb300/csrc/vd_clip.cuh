@@ -20,6 +20,13 @@ namespace vd {
 
 constexpr float kCullPad = 1e-5f;
 
+// Per-warp event counters, kept in shared memory (not registers); uniform
+// events are counted by lane 0, per-lane events with shared atomics.
+struct WarpCounters {
+  unsigned long long cand, clips, nodes, vtests, newv;
+  unsigned fp64, fp64amb, refv, refvol;
+};
+
 template <int VPL, int PCAP, int QPL>
 struct WarpSmem {
   float4 pl[PCAP];   // n^x, n^y, n^z, b^ (local frame)
@@ -33,6 +40,10 @@ struct WarpSmem {
   float qlb[32 * QPL];
   int qref[32 * QPL];
   int qocc[32 * QPL];
+  float rtab[64];          // cell radius per occupied-octant mask
+  int anchor[PCAP];        // FP64 integration: one vertex per face
+  double vd64[3 * 32 * VPL];  // FP64 integration: vertex positions
+  WarpCounters ct;
 };
 
 struct Counters {
@@ -52,7 +63,7 @@ struct Cell {
   uint32_t vt[VPL];
   // warp-uniform state
   float4 me;
-  float lo[3], hi[3];  // the set's box
+  const float* box;  // the set's box: lo[3] then hi[3] (global memory)
   float alo[3], ahi[3];
   float sc[3], srad;  // bounding sphere of the cell (local frame)
   int nv;
@@ -84,9 +95,8 @@ __device__ __forceinline__ PlaneT<double> plane64(int id, const float4& me, cons
 
 // FP64 re-evaluation of "vertex tri lies outside the plane of site hpid".
 template <int VPL, int PCAP, int QPL>
-static __device__ __noinline__ bool resolve64(const WarpSmem<VPL, PCAP, QPL>& S, uint32_t tri, int hpid, float4 me,
-                                       const float* lo, const float* hi, const float4* __restrict__ sites,
-                                       long long& amb) {
+static __device__ __noinline__ bool resolve64(WarpSmem<VPL, PCAP, QPL>& S, uint32_t tri, int hpid, float4 me,
+                                              const float* lo, const float* hi, const float4* __restrict__ sites) {
   PlaneT<double> A = plane64(S.pid[tri & 255u], me, lo, hi, sites);
   PlaneT<double> B = plane64(S.pid[(tri >> 8) & 255u], me, lo, hi, sites);
   PlaneT<double> C = plane64(S.pid[(tri >> 16) & 255u], me, lo, hi, sites);
@@ -94,7 +104,7 @@ static __device__ __noinline__ bool resolve64(const WarpSmem<VPL, PCAP, QPL>& S,
   vertex3<double>(A, B, C, x, y, z, e);
   PlaneT<double> H = plane64(hpid, me, lo, hi, sites);
   double s = side<double>(H, x, y, z);
-  if (ambiguous<double>(s, e, H.e)) amb++;
+  if (ambiguous<double>(s, e, H.e)) atomicAdd(&S.ct.fp64amb, 1u);
   return s > 0.0;
 }
 
@@ -141,8 +151,17 @@ __device__ __forceinline__ float cell_radius(int occ, const float* alo, const fl
   return R;
 }
 
+// Cell radius for each of the 64 occupied-octant masks (see cell_radius),
+// refreshed whenever the cell's bounds change so that node tests and queue
+// re-tests are one table lookup.
+__device__ __forceinline__ void fill_rtab(float* rtab, const float* alo, const float* ahi, const float* sc, float srad,
+                                          int cull_mode) {
+  for (int o = (int)lane_id(); o < 64; o += 32) rtab[o] = cell_radius(o, alo, ahi, sc, srad, cull_mode);
+  __syncwarp();
+}
+
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c) {
+__device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int cull_mode) {
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, em = 0.0f;
 #pragma unroll
   for (int r = 0; r < VPL; r++)
@@ -170,6 +189,7 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c) {
       r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
   c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
+  fill_rtab(S.rtab, c.alo, c.ahi, c.sc, c.srad, cull_mode);
 }
 
 // Test of one BVH child box [lo.xyz, hi.xyz] with maximum weight lo.w
@@ -180,9 +200,8 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c) {
 // dmin, dmax)) (tighter than the paper's dmin/2 for heavy sites). Culled
 // iff LB exceeds the cell radius over the octants the box occupies.
 // Returns keep; lb is a safe (padded) LB, key the best-first key LB - R.
-__device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* alo, const float* ahi,
-                                          const float* sc, float srad, int cull_mode, float& lb, int& occ,
-                                          float& key) {
+__device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* rtab, int cull_mode,
+                                          float& lb, int& occ, float& key) {
   float rl[3] = {lo.x - me.x, lo.y - me.y, lo.z - me.z};
   float rh[3] = {hi.x - me.x, hi.y - me.y, hi.z - me.z};
   float d2 = 0.0f, f2 = 0.0f;
@@ -196,7 +215,7 @@ __device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const
     occ |= (rh[k] >= 0.0f ? 1 : 0) << (2 * k);
     occ |= (rl[k] <= 0.0f ? 1 : 0) << (2 * k + 1);
   }
-  float R = cell_radius(occ, alo, ahi, sc, srad, cull_mode);
+  float R = rtab[occ];
   float c = me.w - lo.w;
   float D = sqrtf(d2);
   if (c > 0.0f) D = fminf(fmaxf(sqrtf(c), D), sqrtf(f2) * (1.0f + kCullPad));
@@ -249,7 +268,7 @@ __device__ __forceinline__ bool queue_pop(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL,
       lb = S.qlb[i];
       rf = S.qref[i];
       oc = S.qocc[i];
-      float R = cell_radius(oc & 63, c.alo, c.ahi, c.sc, c.srad, cull_mode);
+      float R = S.rtab[oc & 63];
       ok = cull_mode == 2 || !(lb > R * (1.0f + kCullPad));
       key = traversal == 0 ? f2o(lb - R) : (0xfffffffeu - (uint32_t)(oc >> 8));
     }
@@ -291,7 +310,7 @@ enum { OVF_QUEUE = 0, OVF_VERTICES = 1, OVF_PLANES = 2, OVF_NEIGHBORS = 3 };
 // Clip the cell by plane H of site hpid (App. B "Clipping by a half-space").
 template <int VPL, int PCAP, int QPL>
 __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, const PlaneT<float>& H, int hpid,
-                         const float4* __restrict__ sites, Counters& ct, bool counters) {
+                         const float4* __restrict__ sites, bool counters) {
   constexpr int VCAP = Cell<VPL, PCAP, QPL>::VCAP;
   constexpr int NPW = Cell<VPL, PCAP, QPL>::NPW;
   const unsigned lane = lane_id(), lt = lanemask_lt();
@@ -304,12 +323,12 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, c
       float s = side<float>(H, c.vx[r], c.vy[r], c.vz[r]);
       out[r] = s > 0.0f;
       if (ambiguous<float>(s, c.ve[r], H.e)) {
-        ct.fp64++;
-        out[r] = resolve64(S, c.vt[r], hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
+        atomicAdd(&S.ct.fp64, 1u);
+        out[r] = resolve64(S, c.vt[r], hpid, c.me, c.box, c.box + 3, sites);
       }
     }
   }
-  if (counters) ct.vtests += c.nv;
+  if (counters && lane == 0) S.ct.vtests += c.nv;
   uint32_t om[VPL];
   int k = 0;
 #pragma unroll
@@ -396,8 +415,8 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, c
         float x, y, z, ev;
         vertex3<float>(A, B, H, x, y, z, ev);
         if (!(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
-          refine_vertex(S.pid[a], S.pid[b], hpid, c.me, c.lo, c.hi, sites, x, y, z, ev);
-          ct.refv++;
+          refine_vertex(S.pid[a], S.pid[b], hpid, c.me, c.box, c.box + 3, sites, x, y, z, ev);
+          atomicAdd(&S.ct.refv, 1u);
         }
         S.nvp[slot] = make_float4(x, y, z, ev);
         S.nvt[slot] = a | (b << 8) | ((uint32_t)h << 16);
@@ -405,7 +424,7 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, c
     }
     m += __popc(nm);
   }
-  if (counters) ct.newv += m;
+  if (counters && lane == 0) S.ct.newv += m;
   if (c.nv - k + m > VCAP) return CLIP_OVERFLOW;
   __syncwarp();
   // step 4: new vertices take the freed and empty slots
@@ -468,11 +487,11 @@ __device__ __forceinline__ bool candidate_test(float nx, float ny, float nz, flo
 
 // Start a cell as the box: 6 planes, 8 corners (App. B "Initialization").
 template <int VPL, int PCAP, int QPL>
-__device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S) {
+__device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int cull_mode) {
   constexpr int NPW = Cell<VPL, PCAP, QPL>::NPW;
   const unsigned lane = lane_id();
   if (lane < 6) {
-    PlaneT<float> B = box_plane<float>((int)lane, c.me.x, c.me.y, c.me.z, c.lo, c.hi);
+    PlaneT<float> B = box_plane<float>((int)lane, c.me.x, c.me.y, c.me.z, c.box, c.box + 3);
     S.pl[lane] = make_float4(B.nx, B.ny, B.nz, B.b);
     S.pe[lane] = B.e;
     S.pid[lane] = -1 - (int)lane;
@@ -499,7 +518,7 @@ __device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL,
   c.qn = 0;
   c.seq = 0;
   c.dirty = false;
-  recompute_aabb(c);
+  recompute_aabb(c, S, cull_mode);
 }
 
 // Compact the vertices into shared memory (S.nvp / S.nvt, in slot order),
@@ -569,14 +588,31 @@ __device__ __forceinline__ void vertex64(uint32_t a, uint32_t b, uint32_t c, con
 }
 
 // Volume and first moment about c of the register-path polytope gathered in
-// S.nvt (slot order, nv vertices), every vertex re-solved in FP64 from the
-// original inputs: the same fan tetrahedra as the FP32 integration.
+// S.nvt (slot order, nv vertices), in FP64: every vertex is re-solved once
+// from the original inputs (kept in S.vd64), and each face's fan is anchored
+// at one of its own vertices (its lowest index), so the integration uses no
+// point that is not a vertex of the cell.
 template <int VPL, int PCAP, int QPL>
-__device__ __noinline__ void volume_fp64(const WarpSmem<VPL, PCAP, QPL>& S, int nv, float4 me, const float* lo,
+__device__ __noinline__ void volume_fp64(WarpSmem<VPL, PCAP, QPL>& S, int nv, float4 me, const float* lo,
                                          const float* hi, const float4* __restrict__ sites, double cx, double cy,
                                          double cz, double& V, double& Mx, double& My, double& Mz) {
+  const unsigned lane = lane_id();
+  for (int f = (int)lane; f < PCAP; f += 32) S.anchor[f] = 0x7fffffff;
+  __syncwarp();
+  for (int t = (int)lane; t < nv; t += 32) {
+    uint32_t T = S.nvt[t];
+    double x, y, z;
+    vertex64(T & 255u, (T >> 8) & 255u, (T >> 16) & 255u, S.pid, me, lo, hi, sites, x, y, z);
+    S.vd64[3 * t] = x - cx;
+    S.vd64[3 * t + 1] = y - cy;
+    S.vd64[3 * t + 2] = z - cz;
+    atomicMin(&S.anchor[T & 255u], t);
+    atomicMin(&S.anchor[(T >> 8) & 255u], t);
+    atomicMin(&S.anchor[(T >> 16) & 255u], t);
+  }
+  __syncwarp();
   V = Mx = My = Mz = 0.0;
-  for (int it = (int)lane_id(); it < 3 * nv; it += 32) {
+  for (int it = (int)lane; it < 3 * nv; it += 32) {
     int t = it / 3, rho = it % 3;
     uint32_t T = S.nvt[t];
     uint32_t U = T | (T << 24);
@@ -585,25 +621,17 @@ __device__ __noinline__ void volume_fp64(const WarpSmem<VPL, PCAP, QPL>& S, int 
     uint32_t q = fy | (fx << 8);
     int u = 0;
     while (u < nv && !tri_has_pair(S.nvt[u], q)) u++;
-    if (u >= nv) continue;
-    uint32_t T2 = S.nvt[u];
-    double ax, ay, az, bx, by, bz;
-    vertex64(T & 255u, (T >> 8) & 255u, (T >> 16) & 255u, S.pid, me, lo, hi, sites, ax, ay, az);
-    vertex64(T2 & 255u, (T2 >> 8) & 255u, (T2 >> 16) & 255u, S.pid, me, lo, hi, sites, bx, by, bz);
-    PlaneT<double> pf = plane64(S.pid[fy], me, lo, hi, sites);
-    double hgt = pf.nx * cx + pf.ny * cy + pf.nz * cz - pf.b;
-    double gx = -hgt * pf.nx, gy = -hgt * pf.ny, gz = -hgt * pf.nz;
-    ax -= cx;
-    ay -= cy;
-    az -= cz;
-    bx -= cx;
-    by -= cy;
-    bz -= cz;
-    double det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
+    int g = S.anchor[fy];
+    if (u >= nv || g == t || g == u) continue;  // triangles through the anchor vanish
+    const double* A = &S.vd64[3 * g];
+    const double* B = &S.vd64[3 * t];
+    const double* C = &S.vd64[3 * u];
+    double det = A[0] * (B[1] * C[2] - B[2] * C[1]) + A[1] * (B[2] * C[0] - B[0] * C[2]) +
+                 A[2] * (B[0] * C[1] - B[1] * C[0]);
     V += det;
-    Mx += det * (gx + ax + bx);
-    My += det * (gy + ay + by);
-    Mz += det * (gz + az + bz);
+    Mx += det * (A[0] + B[0] + C[0]);
+    My += det * (A[1] + B[1] + C[1]);
+    Mz += det * (A[2] + B[2] + C[2]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -616,6 +644,7 @@ __device__ __noinline__ void volume_fp64(const WarpSmem<VPL, PCAP, QPL>& S, int 
   Mx /= 24.0;
   My /= 24.0;
   Mz /= 24.0;
+  __syncwarp();
 }
 
 }  // namespace vd

@@ -30,6 +30,7 @@ constexpr int kNaWarps = 4;
 
 struct NoAllocScratch {
   float4 sites[kNaMaxSites];         // packed (x, y, z, w), by site index
+  float box[6];                      // lo[3], hi[3]
   unsigned char loser[kNaMaxSites];  // an exact duplicate site beats this one
   int work;                          // persistent-grid work counter
   int error;                         // first device-side error
@@ -43,8 +44,9 @@ static __device__ __align__(256) unsigned char g_scratch[sizeof(NoAllocScratch)]
 using Smem = WarpSmem<kNaVpl, kNaPcap, 1>;
 using CellT = Cell<kNaVpl, kNaPcap, 1>;
 
-__global__ void na_pack_kernel(const float* __restrict__ xyz, const float* __restrict__ w, int n,
+__global__ void na_pack_kernel(const float* __restrict__ xyz, const float* __restrict__ w, int n, vd_box box,
                                NoAllocScratch* S) {
+  if (blockIdx.x == 0 && threadIdx.x < 6) S->box[threadIdx.x] = threadIdx.x < 3 ? box.lo[threadIdx.x] : box.hi[threadIdx.x - 3];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     float wi = w ? w[i] : 0.0f;
@@ -62,7 +64,7 @@ __global__ void na_pack_kernel(const float* __restrict__ xyz, const float* __res
 }
 
 // One warp per cell, every other site a candidate.
-__global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box box, int32_t* __restrict__ counts,
+__global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t* __restrict__ counts,
                                                                  int32_t* __restrict__ nbrs,
                                                                  float* __restrict__ vol, float* __restrict__ cen,
                                                                  NoAllocScratch* SC) {
@@ -70,7 +72,8 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box b
   Smem& S = smem[threadIdx.x >> 5];
   const unsigned lane = lane_id(), lt = lanemask_lt();
   const float4* __restrict__ sites = SC->sites;
-  Counters ct = {};
+  if (lane == 0) S.ct = WarpCounters{};
+  __syncwarp();
   while (true) {
     int i = 0;
     if (lane == 0) i = atomicAdd(&SC->work, 1);
@@ -78,13 +81,9 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box b
     if (i >= n) break;
     CellT c;
     c.me = sites[i];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      c.lo[k] = box.lo[k];
-      c.hi[k] = box.hi[k];
-    }
+    c.box = SC->box;
     bool empty = SC->loser[i] != 0, overflow = false;
-    if (!empty) init_cell(c, S);
+    if (!empty) init_cell(c, S, 0);
     for (int base = 0; base < n && !empty && !overflow; base += 32) {
       const int j = base + (int)lane;
       bool keep = false;
@@ -119,7 +118,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box b
         Hb.e = __shfl_sync(FULL, H.e, src);
         if ((int)lane == src) keep = false;
         km &= ~(1u << src);
-        int rc = clip_cell(c, S, Hb, base + src, sites, ct, false);
+        int rc = clip_cell(c, S, Hb, base + src, sites, false);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box b
         if (rc == CLIP_DONE) c.dirty = true;
       }
       if (c.dirty && !empty && !overflow) {
-        recompute_aabb(c);
+        recompute_aabb(c, S, 0);
         c.dirty = false;
       }
     }
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, vd_box b
     double ox = cx, oy = cy, oz = cz, Vd = V;
     if (volume_needs_fp64(V, L, Sabs, emax)) {
       double Mxd, Myd, Mzd;
-      volume_fp64(S, nv, c.me, c.lo, c.hi, sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
+      volume_fp64(S, nv, c.me, c.box, c.box + 3, sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
       if (Vd > 0.0) {
         ox += Mxd / Vd;
         oy += Myd / Vd;
@@ -284,13 +283,13 @@ extern "C" int vd_cells_noalloc(const float* sites_xyz, const float* weights, in
   // the work counter and the error word must start at zero on every call
   if (cudaMemsetAsync(&S->work, 0, 2 * sizeof(int), s) != cudaSuccess) return VD_ERR_CUDA;
   int nn = (int)n;
-  na_pack_kernel<<<(nn + 255) / 256, 256, 0, s>>>(sites_xyz, weights, nn, S);
+  na_pack_kernel<<<(nn + 255) / 256, 256, 0, s>>>(sites_xyz, weights, nn, bbox, S);
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int blocks = (nn + kNaWarps - 1) / kNaWarps;
   if (sms > 0 && blocks > 4 * sms) blocks = 4 * sms;
-  na_cells_kernel<<<blocks, 32 * kNaWarps, 0, s>>>(nn, bbox, counts, neighbors, volume, centroid, S);
+  na_cells_kernel<<<blocks, 32 * kNaWarps, 0, s>>>(nn, counts, neighbors, volume, centroid, S);
   na_status_kernel<<<1, 1, 0, s>>>(S, status);
   return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
 }

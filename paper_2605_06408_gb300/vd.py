@@ -58,6 +58,7 @@ class VdConfig(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("counters", ctypes.c_int32),
         ("timing", ctypes.c_int32),
+        ("warm_start", ctypes.c_int32),
     ]
 
 
