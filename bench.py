@@ -43,6 +43,9 @@ WORKLOADS = {
                    "full ncu captures",
     "surfaces20M": "Voronoi of 20,000,000 sites in nested Gaussian shells (sigma 1e-2..1e-5) around 32 "
                    "random surfaces + 1% background, seed 4",
+    "batched256": "256 independent sets, sizes log-uniform in [1e3, 2e5] (~9M sites), odd sets power "
+                  "(w = r^2, r = 0.2 nn exp(N(0,1))), uniform or mixture per set, seed 3; one build_batched "
+                  "per step, replayed from a CUDA graph",
 }
 
 # algorithmic FP32 work per counted event ("Roofline"):
@@ -75,9 +78,21 @@ def dist_env():
 
 
 def make_workload(name: str, rank: int):
+    """(xyz, weights or None, box, batch) where batch = (set offsets, boxes,
+    weighted flags) for batched workloads, else None."""
     from paper_2605_06408_gb300 import workloads as W
 
     seed_shift = 1000 * rank  # independent point sets per rank
+    if name == "batched256":
+        X, Wt, offs, flags = W.batched(3 + seed_shift)
+        return X, Wt, W.UNIT_BOX, (offs, [W.UNIT_BOX] * (len(offs) - 1), flags)
+    x, w, box = _single_workload(name, seed_shift)
+    return x, w, box, None
+
+
+def _single_workload(name: str, seed_shift: int):
+    from paper_2605_06408_gb300 import workloads as W
+
     if name == "mixture1M":
         return W.mixture(1_000_000, 1 + seed_shift), None, W.UNIT_BOX
     if name == "power1M":
@@ -166,7 +181,11 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    x, w, box = make_workload(args.workload, 0)
+    x, w, box, batch = make_workload(args.workload, 0)
+    if batch is not None:  # the oracle builds each set on its own: sample the largest set
+        offs = batch[0]
+        s = int(np.argmax(np.diff(offs)))
+        x, w = x[offs[s]:offs[s + 1]], (w[offs[s]:offs[s + 1]] if batch[2][s] else None)
     sample = min(args.cpu_sample // 3, len(x))
     for _ in range(args.warmup):
         cpu_oracle_rate(x, w, box, min(sample, 20_000))
@@ -227,7 +246,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_2605_06408_gb300 import vd
 
-    x, w, box = make_workload(args.workload, rank)
+    x, w, box, batch = make_workload(args.workload, rank)
     n = len(x)
     cfg = {"timing": 1}
     if args.config:
@@ -238,17 +257,22 @@ def run_ours(args):
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
+    def build(c, xs, wts, cap=None, sync=True):
+        if batch is None:
+            return c.build(xs, wts, box, nnz_capacity=cap, sync=sync)
+        return c.build_batched(xs, wts, batch[0], batch[1], batch[2], nnz_capacity=cap, sync=sync)
+
     # warm-up (also sizes the workspace and the neighbour buffer)
     res = None
     for _ in range(max(args.warmup, 1)):
-        res = ctx.build(sites, weights, box)
+        res = build(ctx, sites, weights)
     nnz = res.nnz
     cap = nnz + 1024
     st = ctx.status()
 
     # algorithmic work of one build, from a separate counting run
     cctx = vd.Context(local, dict(cfg, counters=1))
-    cctx.build(sites, weights, box)
+    build(cctx, sites, weights)
     cnt = cctx.status()
     flop = (FLOP_VTEST * cnt["vertex_tests"] + FLOP_NEWV * cnt["new_vertices"] + FLOP_CAND * cnt["candidates"]
             + FLOP_NODE * cnt["nodes"])
@@ -264,17 +288,48 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     sampler.start()
+    graph = None
+    if batch is not None:
+        # batched steps replay one captured launch sequence (vd_build_batched
+        # enqueues kernels, async copies and memsets only)
+        gctx = vd.Context(local, dict(cfg, timing=0))
+        gctx.reserve(n, weights is not None)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            build(gctx, sites, weights, cap, sync=False)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            build(gctx, sites, weights, cap, sync=False)
+        graph.replay()
+        torch.cuda.synchronize()
+        g_launches = gctx.timings()["launches"]
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if graph is not None:
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            launches += g_launches
+            continue
         e0.record(stream)
-        ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+        build(ctx, sites, weights, cap, sync=False)
         e1.record(stream)
         t = ctx.timings()  # synchronises the stream
         step_ms.append(e0.elapsed_time(e1))
         cells_ms.append(t["cells_ms"])
         launches += t["launches"]
+    if graph is not None:  # the fused kernel's time from an eager build with events
+        for _ in range(2):
+            flush.zero_()
+            build(ctx, sites, weights, cap, sync=False)
+            cells_ms.append(ctx.timings()["cells_ms"])
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
@@ -288,7 +343,7 @@ def run_ours(args):
         c, d = W.loss_coefficients(n, 4)
         gv = torch.from_numpy(c).float().to(dev)
         gc = torch.from_numpy(d).float().to(dev)
-        ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+        build(ctx, sites, weights, cap, sync=False)
         ctx.backward(gv, gc, want_weights=weights is not None)
         torch.cuda.synchronize()
         fb = []
@@ -298,7 +353,7 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.build(sites, weights, box, nnz_capacity=cap, sync=False)
+            build(ctx, sites, weights, cap, sync=False)
             ctx.backward(gv, gc, want_weights=weights is not None)
             e1.record(stream)
             e1.synchronize()
@@ -325,7 +380,7 @@ def run_ours(args):
         d_sites.copy_(h_sites, non_blocking=True)
         if d_w is not None:
             d_w.copy_(h_w, non_blocking=True)
-        r = ctx.build(d_sites, d_w, box, nnz_capacity=cap, sync=False)
+        r = build(ctx, d_sites, d_w, cap, sync=False)
         h_off.copy_(r.offsets, non_blocking=True)
         h_nb.copy_(r.neighbors[:nnz], non_blocking=True)
         h_vol.copy_(r.volume, non_blocking=True)
@@ -367,7 +422,13 @@ def run_ours(args):
 
     cpu = None
     if not args.no_cpu_baseline:
-        rate, cores, dt, m = cpu_oracle_rate(x, w, box, args.cpu_sample)
+        cx, cw = x, w
+        if batch is not None:  # the oracle builds each set on its own: sample the largest set
+            offs = batch[0]
+            s_big = int(np.argmax(np.diff(offs)))
+            cx = x[offs[s_big]:offs[s_big + 1]]
+            cw = w[offs[s_big]:offs[s_big + 1]] if batch[2][s_big] else None
+        rate, cores, dt, m = cpu_oracle_rate(cx, cw, box, args.cpu_sample)
         cpu = {"value": rate, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
                "sample": f"{m} seeded cells of {args.workload} ({dt:.1f} s, FP64 k-d tree oracle, all host cores)"}
 
@@ -386,6 +447,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": n,
                    "weighted": w is not None, "l2": "flushed between timed steps (256 MiB write)",
+                   "timed_step": "CUDA graph replay" if graph is not None else "eager vd_build",
                    "libvd": {k: v for k, v in ctx.config.items()}},
         "fwd_bwd_mcells_s": None if fb_ms is None else total_cells / (fb_ms * 1e-3) / 1e6,
         "fwd_bwd_ms_per_step": fb_ms,

@@ -1,0 +1,122 @@
+"""Full-size configurations through the C ABI, checked on sampled cells
+against the FP64 oracle: the batched build (256 sets, ~9M sites) eager and
+replayed from a CUDA graph, the adjoint at 1M sites, and the 20M-site
+surface set (forward + adjoint)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_06408_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vdmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_06408_gb300 import vd
+
+    vd.load_library()
+    return vd
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def check_rows(off, nb, vol, cen, ref, cells, base=0):
+    for q, i in enumerate(cells):
+        assert np.array_equal(nb[off[base + i]:off[base + i + 1]], ref["nbrs"][q]), (base, i)
+    rv = ref["vol"]
+    gv = vol[base + cells].astype(np.float64)
+    assert np.all(np.abs(gv - rv) <= 1e-5 * rv + 1e-30)
+    gc = cen[base + cells].astype(np.float64)
+    assert np.all(np.linalg.norm(gc - ref["cen"], axis=1) <= 1e-5 * np.linalg.norm(ref["cen"], axis=1))
+
+
+def test_batched_256_sets_eager_and_graph(vdmod):
+    X, Wt, offs, flags = W.batched(3)
+    boxes = [W.UNIT_BOX] * (len(offs) - 1)
+    ctx = vdmod.Context(0)
+    r = ctx.build_batched(dev(X), dev(Wt), offs, boxes, flags)
+    st = ctx.status()
+    assert st["error"] == 0 and st["failed_cells"] == 0
+    off = r.offsets.cpu().numpy().astype(np.int64)
+    nb = r.neighbors.cpu().numpy()
+    vol = r.volume.cpu().numpy()
+    cen = r.centroid.cpu().numpy()
+    for s in (0, 1, 2, 3, 128, 254, 255):
+        a, b = int(offs[s]), int(offs[s + 1])
+        cells = np.arange(b - a) if b - a <= 2000 else np.sort(W.rng_for(s).choice(b - a, 2000, replace=False))
+        ref = oracle.cells(X[a:b], Wt[a:b] if flags[s] else None, W.UNIT_BOX, cells=cells)
+        check_rows(off, nb, vol, cen, ref, cells, base=a)
+    # the same build captured once into a CUDA graph and replayed
+    n = len(X)
+    g_ctx = vdmod.Context(0)
+    g_ctx.reserve(n, True)
+    xs, ws = dev(X), dev(Wt)
+    cap = r.nnz + 1024
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        g_ctx.build_batched(xs, ws, offs, boxes, flags, nnz_capacity=cap, sync=False)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rg = g_ctx.build_batched(xs, ws, offs, boxes, flags, nnz_capacity=cap, sync=False)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(rg.offsets, r.offsets)
+    assert torch.equal(rg.neighbors[: r.nnz], r.neighbors)
+    assert torch.allclose(rg.volume, r.volume, rtol=1e-6, atol=0)
+
+
+def _grad_subset_check(x, w, res, gp, gw, c, d, k=200, seed=9):
+    off = res.offsets.cpu().numpy().astype(np.int64)
+    nb = res.neighbors.cpu().numpy()
+    K = np.sort(W.rng_for(seed).choice(len(x), k, replace=False))
+    K = K[np.diff(off)[K] > 0]
+    cells = np.unique(np.concatenate([K] + [nb[off[q]:off[q + 1]] for q in K]))
+    ogp, ogw, _ = oracle.grad(x, w, W.UNIT_BOX, c, d, cells=cells)
+    g = gp.cpu().numpy()[K].astype(np.float64)
+    err = np.abs(g - ogp[K]).max(1) / np.maximum(np.abs(ogp[K]).max(1), 1e-30)
+    assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
+    if gw is not None:
+        gww = gw.cpu().numpy()[K].astype(np.float64)
+        ew = np.abs(gww - ogw[K]) / np.maximum(np.abs(ogw[K]), 1e-3 * np.abs(ogw[K]).max())
+        assert np.quantile(ew, 0.99) < 1e-3
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_backward_at_1M(vdmod, weighted):
+    x = W.mixture(1_000_000, 1)
+    w = W.power_weights(x, 2) if weighted else None
+    c, d = W.loss_coefficients(len(x), 4)
+    ctx = vdmod.Context(0)
+    res = ctx.build(dev(x), dev(w), W.UNIT_BOX)
+    gp, gw = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=weighted)
+    assert ctx.status()["error"] == 0
+    _grad_subset_check(x, w, res, gp, gw, c, d)
+
+
+def test_surfaces_20M_forward_and_backward(vdmod):
+    x = W.surfaces(20_000_000, 4)
+    ctx = vdmod.Context(0)
+    res = ctx.build(dev(x), None, W.UNIT_BOX)
+    st = ctx.status()
+    assert st["error"] == 0 and st["failed_cells"] == 0
+    off = res.offsets.cpu().numpy().astype(np.int64)
+    nb = res.neighbors.cpu().numpy()
+    samp = np.sort(W.rng_for(11).choice(len(x), 1500, replace=False))
+    ref = oracle.cells(x, None, W.UNIT_BOX, cells=samp)
+    check_rows(off, nb, res.volume.cpu().numpy(), res.centroid.cpu().numpy(), ref, samp)
+    # volumes partition the box at any size
+    assert res.volume.double().sum().item() == pytest.approx(1.0, rel=1e-5)
+    c, d = W.loss_coefficients(len(x), 4)
+    gp, _ = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=False)
+    _grad_subset_check(x, None, res, gp, None, c, d, k=150, seed=12)
