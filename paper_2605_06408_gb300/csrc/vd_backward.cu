@@ -397,7 +397,10 @@ cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s) {
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * wpb, smem);
   if (err != cudaSuccess) return err;
   kern<<<num_sms * (occ > 0 ? occ : 1), 32 * wpb, smem, s>>>(b);
-  big_back_kernel<<<num_sms, 32 * kBigWarpsPerBlock, 0, s>>>(b);
+  const size_t big_smem = kBigSmemPerWarp * kBigWarpsPerBlock;
+  err = cudaFuncSetAttribute(big_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+  if (err != cudaSuccess) return err;
+  big_back_kernel<<<num_sms, 32 * kBigWarpsPerBlock, big_smem, s>>>(b);
   return cudaGetLastError();
 }
 

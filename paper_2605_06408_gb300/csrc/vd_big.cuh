@@ -8,6 +8,18 @@
 // per-thread state in global memory (App. A.3). Planes are compacted when
 // the plane array passes 85% occupancy (App. A.4). Plane indices are 16-bit,
 // vertex triplets 64-bit (a | b<<16 | c<<32, bit 63 = "outside" mark).
+//
+// Cells of large-weight sites reach thousands of vertices while almost all
+// of their candidates (>99% on log-normal weights) cut nothing; each such
+// candidate would otherwise test every vertex. The vertex array is therefore
+// covered by chunk boxes (32 consecutive vertices each, with their largest
+// error bound), rebuilt after every clip, and the read-only first pass tests
+// a chunk's vertices only when the plane reaches the chunk's box. To keep
+// the chunks compact, the vertex array of a large polytope is re-sorted after
+// every clip by the cube-map cell of its direction from the polytope's box
+// centre (6 faces x 8 x 8 cells, Morton order within a face), so a chunk is a
+// small patch of the surface and a plane that passes close to the polytope
+// reaches the boxes of only a few patches.
 #pragma once
 
 #include "vd_clip.cuh"
@@ -18,6 +30,7 @@ constexpr int kBigV = 16384;   // vertices per cell
 constexpr int kBigP = 8192;    // planes per cell
 constexpr int kBigQ = 8192;    // queue entries
 constexpr int kBigH = 65536;   // pair-hash slots (power of two)
+constexpr int kBigC = kBigV / 32;  // chunk boxes
 constexpr int kBigGc = (kBigP * 85) / 100;
 constexpr uint64_t kBigOut = 1ull << 63;
 constexpr uint64_t kTriMask = 0x0000ffffffffffffull;
@@ -33,22 +46,33 @@ struct BigArena {
   uint64_t* otri;
   float4* nvp;
   uint64_t* nvt;
-  float* qlb;
-  int* qref;
-  int* qocc;
+  int4* q;  // best-first queue: 32-ary min-heap of (key, lb, ref, occ)
   uint32_t* hkey;
   int* hval;
   float* acc;
   float* rtab;  // [64] cell radius per occupied-octant mask
+  float4* cb;   // [2 kBigC] chunk q: cb[2q] = (lo, max error), cb[2q+1] = (hi, 0)
+  // shared memory of the warp
+  float4* hs;      // [32] staged candidate planes (n, b)
+  float* hse;      // [32] their error bounds
+  uint32_t* hist;  // [kDirBins] direction-bin counts / cursors
 };
+
+constexpr int kDirBins = 6 * 64;
+// Polytopes of more vertices than this are kept in direction-bin order.
+constexpr int kSortMin = 128;
+
+// Shared memory per warp of the large-cell kernels.
+constexpr size_t kBigSmemPerWarp = 32 * 16 + 32 * 4 + kDirBins * 4;
 
 __host__ __device__ inline size_t big_arena_bytes() {
   size_t b = 64 * 4;
   b += (size_t)kBigP * (16 + 4 + 4 + 4);
   b += (size_t)kBigV * (16 + 8 + 8 + 16 + 8);
-  b += (size_t)kBigQ * 12;
+  b += (size_t)kBigQ * 16;
   b += (size_t)kBigH * 8;
   b += (size_t)kBigP * 10 * 4;
+  b += 64 * 4 + (size_t)kBigC * 32;
   return (b + 255) & ~(size_t)255;
 }
 
@@ -73,12 +97,8 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   p += (size_t)kBigP * 4;
   A.flag = (int*)p;
   p += (size_t)kBigP * 4;
-  A.qlb = (float*)p;
-  p += (size_t)kBigQ * 4;
-  A.qref = (int*)p;
-  p += (size_t)kBigQ * 4;
-  A.qocc = (int*)p;
-  p += (size_t)kBigQ * 4;
+  A.q = (int4*)p;
+  p += (size_t)kBigQ * 16;
   A.hkey = (uint32_t*)p;
   p += (size_t)kBigH * 4;
   A.hval = (int*)p;
@@ -86,6 +106,13 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   A.acc = (float*)p;
   p += (size_t)kBigP * 10 * 4;
   A.rtab = (float*)p;
+  p += 64 * 4;
+  A.cb = (float4*)p;
+  extern __shared__ __align__(16) char big_smem[];
+  char* w = big_smem + (size_t)(threadIdx.x >> 5) * kBigSmemPerWarp;
+  A.hs = (float4*)w;
+  A.hse = (float*)(w + 32 * 16);
+  A.hist = (uint32_t*)(w + 32 * 16 + 32 * 4);
   return A;
 }
 
@@ -163,6 +190,220 @@ __device__ __forceinline__ PlaneT<float> big_plane(const BigArena& A, int k) {
   return P;
 }
 
+// Cube-map cell of direction (dx, dy, dz): face * 64 + Morton(iu, iv) on an
+// 8 x 8 grid of the face.
+__device__ __forceinline__ uint32_t dir_bin(float dx, float dy, float dz) {
+  const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+  uint32_t f;
+  float m, a, b;
+  if (ax >= ay && ax >= az) {
+    f = dx >= 0.0f ? 0u : 1u;
+    m = ax;
+    a = dy;
+    b = dz;
+  } else if (ay >= az) {
+    f = dy >= 0.0f ? 2u : 3u;
+    m = ay;
+    a = dz;
+    b = dx;
+  } else {
+    f = dz >= 0.0f ? 4u : 5u;
+    m = az;
+    a = dx;
+    b = dy;
+  }
+  const float inv = m > 0.0f ? 4.0f / m : 0.0f;
+  const uint32_t iu = (uint32_t)min(7, max(0, (int)fmaf(a, inv, 4.0f)));
+  const uint32_t iv = (uint32_t)min(7, max(0, (int)fmaf(b, inv, 4.0f)));
+  uint32_t mo = 0;
+#pragma unroll
+  for (int k = 0; k < 3; k++) mo |= (((iu >> k) & 1u) << (2 * k)) | (((iv >> k) & 1u) << (2 * k + 1));
+  return f * 64u + mo;
+}
+
+// Stable counting sort of the vertex array by direction bin about the box
+// centre (c.sc), through the staging arrays nvp / nvt.
+__device__ inline void big_sort_vertices(const BigCell& c, const BigArena& A) {
+  const unsigned lane = lane_id(), lt = lanemask_lt();
+  for (int b = (int)lane; b < kDirBins; b += 32) A.hist[b] = 0;
+  __syncwarp();
+  for (int i = (int)lane; i < c.nv; i += 32) {
+    const float4 v = A.vp[i];
+    atomicAdd(&A.hist[dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2])], 1u);
+  }
+  __syncwarp();
+  // exclusive scan: lane l owns bins [12 l, 12 l + 12)
+  {
+    constexpr int per = kDirBins / 32;
+    uint32_t loc[per], sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; k++) {
+      loc[k] = A.hist[per * lane + k];
+      sum += loc[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(FULL, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    uint32_t run = incl - sum;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < per; k++) {
+      A.hist[per * lane + k] = run;
+      run += loc[k];
+    }
+  }
+  __syncwarp();
+  for (int base = 0; base < c.nv; base += 32) {
+    const int i = base + (int)lane;
+    const bool in = i < c.nv;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint64_t T = 0;
+    uint32_t b = 0xffffffffu;
+    if (in) {
+      v = A.vp[i];
+      T = A.vt[i];
+      b = dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2]);
+    }
+    const uint32_t peers = __match_any_sync(FULL, b);
+    const int pos = in ? (int)A.hist[b] + __popc(peers & lt) : 0;
+    __syncwarp();
+    if (in) {
+      A.nvp[pos] = v;
+      A.nvt[pos] = T;
+      if ((peers & lt) == 0) A.hist[b] += __popc(peers);
+    }
+    __syncwarp();
+  }
+  for (int i = (int)lane; i < c.nv; i += 32) {
+    A.vp[i] = A.nvp[i];
+    A.vt[i] = A.nvt[i];
+  }
+  __syncwarp();
+}
+
+// Chunk boxes of the current vertex array (exact min / max of the stored
+// FP32 positions).
+__device__ inline void big_chunk_boxes(const BigCell& c, const BigArena& A) {
+  const int nch = (c.nv + 31) >> 5;
+  for (int q = (int)lane_id(); q < nch; q += 32) {
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, em = 0.0f;
+    const int i1 = min(c.nv, 32 * q + 32);
+#pragma unroll 8
+    for (int i = 32 * q; i < i1; i++) {
+      const float4 v = A.vp[i];
+      lx = fminf(lx, v.x);
+      ly = fminf(ly, v.y);
+      lz = fminf(lz, v.z);
+      hx = fmaxf(hx, v.x);
+      hy = fmaxf(hy, v.y);
+      hz = fmaxf(hz, v.z);
+      em = fmaxf(em, v.w);
+    }
+    A.cb[2 * q] = make_float4(lx, ly, lz, em);
+    A.cb[2 * q + 1] = make_float4(hx, hy, hz, 0.0f);
+  }
+  __syncwarp();
+}
+
+// May plane H leave a vertex of the chunk with box (lo, hi) outside or
+// ambiguous? S = max over the box of n.x - b bounds n.v - b for every
+// vertex v in it; the FP32 evaluations of S and of a vertex's sign test
+// each round by at most 4u (|n|.max|x| + |b|), so a chunk whose S stays
+// below -(2 (emax + e_H) + 8u (...)) holds only vertices the sign test
+// classifies as certainly inside.
+__device__ __forceinline__ bool chunk_may_cut(const PlaneT<float>& H, float4 lo, float4 hi) {
+  const float u = Num<float>::u;
+  const float sx = H.nx >= 0.0f ? hi.x : lo.x, sy = H.ny >= 0.0f ? hi.y : lo.y, sz = H.nz >= 0.0f ? hi.z : lo.z;
+  const float S = fmaf(H.nx, sx, fmaf(H.ny, sy, fmaf(H.nz, sz, -H.b)));
+  const float m1 = fabsf(H.nx) * fmaxf(fabsf(lo.x), fabsf(hi.x)) + fabsf(H.ny) * fmaxf(fabsf(lo.y), fabsf(hi.y)) +
+                   fabsf(H.nz) * fmaxf(fabsf(lo.z), fabsf(hi.z)) + fabsf(H.b);
+  return !(S < -(2.0f * (lo.w + H.e) + 8.0f * u * m1));
+}
+
+// Polytopes of at most this many chunks are scanned without the box stage.
+constexpr int kBoxStage = 2;
+
+// Leaf-batch filter: which of the k <= 32 planes staged in A.hs / A.hse may
+// cut the polytope (some vertex outside or ambiguous)? Bit t of the result
+// stands for plane t. Each vertex chunk is loaded once for all planes whose
+// test reaches its box. A plane that leaves every vertex certainly inside
+// also leaves every later (clipped, smaller) polytope of the cell inside, so
+// the caller drops it for good.
+__device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k, Counters& ct, bool counters) {
+  const unsigned lane = lane_id();
+  uint32_t open = k >= 32 ? FULL : ((1u << k) - 1u);
+  uint32_t cuts = 0;
+  long long tested = 0;
+  const int nch = (c.nv + 31) >> 5;
+  for (int cbase = 0; cbase < nch && open; cbase += 32) {
+    const int q = cbase + (int)lane;
+    uint32_t fl = 0;
+    if (q < nch) {
+      if (nch <= kBoxStage) {
+        fl = open;
+      } else {
+        const float4 lo = A.cb[2 * q], hi = A.cb[2 * q + 1];
+        for (uint32_t m = open; m; m &= m - 1) {
+          const int t = __ffs(m) - 1;
+          const float4 h = A.hs[t];
+          PlaneT<float> H;
+          H.nx = h.x;
+          H.ny = h.y;
+          H.nz = h.z;
+          H.b = h.w;
+          H.e = A.hse[t];
+          if (chunk_may_cut(H, lo, hi)) fl |= 1u << t;
+        }
+      }
+    }
+    uint32_t U = __ballot_sync(FULL, fl != 0);
+    while (U && open) {
+      // up to four flagged chunks per step, their vertex loads in flight together
+      int qs[4];
+      uint32_t pms[4];
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        qs[u] = U ? __ffs(U) - 1 : -1;
+        U &= U ? U - 1 : 0u;
+        pms[u] = __shfl_sync(FULL, fl, qs[u] < 0 ? 0 : qs[u]) & open;
+        if (qs[u] < 0) pms[u] = 0;
+        const int i = 32 * (cbase + (qs[u] < 0 ? 0 : qs[u])) + (int)lane;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pms[u] && i < c.nv) v[u] = A.vp[i];
+      }
+      uint32_t outm = 0;
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int i = 32 * (cbase + (qs[u] < 0 ? 0 : qs[u])) + (int)lane;
+        if (i < c.nv) {
+          for (uint32_t m = pms[u]; m; m &= m - 1) {
+            const int t = __ffs(m) - 1;
+            const float4 h = A.hs[t];
+            PlaneT<float> H;
+            H.nx = h.x;
+            H.ny = h.y;
+            H.nz = h.z;
+            H.b = h.w;
+            H.e = A.hse[t];
+            const float s = side<float>(H, v[u].x, v[u].y, v[u].z);
+            if (s > 0.0f || ambiguous<float>(s, v[u].w, H.e)) outm |= 1u << t;
+          }
+        }
+        tested += 32 * __popc(pms[u]);
+      }
+      outm = __reduce_or_sync(FULL, outm);
+      cuts |= outm;
+      open &= ~outm;
+    }
+  }
+  if (counters) ct.vtests += tested;
+  return cuts;
+}
+
 __device__ inline void big_aabb(BigCell& c, const BigArena& A, int cull_mode) {
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY}, em = 0.0f;
   for (int i = (int)lane_id(); i < c.nv; i += 32) {
@@ -220,6 +461,7 @@ __device__ inline void big_init(BigCell& c, const BigArena& A, int cull_mode) {
   c.seq = 0;
   c.dirty = false;
   __syncwarp();
+  big_chunk_boxes(c, A);
   big_aabb(c, A, cull_mode);
 }
 
@@ -291,50 +533,79 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
   const unsigned lane = lane_id(), lt = lanemask_lt();
   if (c.npl >= kBigGc) big_gc(c, A);
   if (c.npl >= kBigP) return CLIP_OVERFLOW;
-  // read-only first pass (four independent loads per lane in flight): most
+  // read-only first pass over the chunks whose box the plane reaches; most
   // candidates cut nothing and end here without writes
   {
     bool any = false;
-    for (int base = 0; base < c.nv && !any; base += 128) {
-      bool o = false;
+    const int nch = (c.nv + 31) >> 5;
+    long long tested = 0;
+    for (int cbase = 0; cbase < nch && !any; cbase += 32) {
+      const int q = cbase + (int)lane;
+      bool f = q < nch;
+      if (f && nch > kBoxStage) f = chunk_may_cut(H, A.cb[2 * q], A.cb[2 * q + 1]);
+      uint32_t fm = __ballot_sync(FULL, f);
+      while (fm && !any) {
+        // up to four flagged chunks per step, their loads in flight together
+        int qs[4];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        int i = base + 32 * u + (int)lane;
-        if (i < c.nv) {
-          float4 v = A.vp[i];
-          float s = side<float>(H, v.x, v.y, v.z);
-          bool out = s > 0.0f;
-          if (ambiguous<float>(s, v.w, H.e)) out = true;  // settled in FP64 by the marking pass
-          o = o || out;
+        for (int u = 0; u < 4; u++) {
+          qs[u] = fm ? cbase + __ffs(fm) - 1 : -1;
+          fm &= fm - 1;
         }
+        bool o = false;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int i = 32 * qs[u] + (int)lane;
+          if (qs[u] >= 0 && i < c.nv) {
+            float4 v = A.vp[i];
+            float s = side<float>(H, v.x, v.y, v.z);
+            bool out = s > 0.0f;
+            if (ambiguous<float>(s, v.w, H.e)) out = true;  // settled in FP64 by the marking pass
+            o = o || out;
+          }
+          tested += qs[u] >= 0 ? 32 : 0;
+        }
+        any = __any_sync(FULL, o);
       }
-      any = __any_sync(FULL, o);
     }
-    if (counters) ct.vtests += c.nv;
+    if (counters) ct.vtests += tested;
     if (!any) return CLIP_NONE;
   }
-  // classify; mark outside vertices and list their triplets
+  // classify; mark outside vertices and list their triplets (four rows of
+  // loads in flight per step)
   int k = 0;
-  for (int base = 0; base < c.nv; base += 32) {
-    int i = base + (int)lane;
-    bool out = false;
-    uint64_t T = 0;
-    if (i < c.nv) {
-      float4 v = A.vp[i];
-      T = A.vt[i];
-      float s = side<float>(H, v.x, v.y, v.z);
-      out = s > 0.0f;
-      if (ambiguous<float>(s, v.w, H.e)) {
-        ct.fp64++;
-        out = big_resolve64(A, T, hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
+  for (int base = 0; base < c.nv; base += 128) {
+    float4 v[4];
+    uint64_t T[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = base + 32 * u + (int)lane;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      T[u] = 0;
+      if (i < c.nv) {
+        v[u] = A.vp[i];
+        T[u] = A.vt[i];
       }
     }
-    uint32_t m = __ballot_sync(FULL, out);
-    if (out) {
-      A.otri[k + __popc(m & lt)] = T;
-      A.vt[i] = T | kBigOut;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = base + 32 * u + (int)lane;
+      bool out = false;
+      if (i < c.nv) {
+        float s = side<float>(H, v[u].x, v[u].y, v[u].z);
+        out = s > 0.0f;
+        if (ambiguous<float>(s, v[u].w, H.e)) {
+          ct.fp64++;
+          out = big_resolve64(A, T[u], hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
+        }
+      }
+      uint32_t m = __ballot_sync(FULL, out);
+      if (out) {
+        A.otri[k + __popc(m & lt)] = T[u];
+        A.vt[i] = T[u] | kBigOut;
+      }
+      k += __popc(m);
     }
-    k += __popc(m);
   }
   __syncwarp();
   if (k == 0) return CLIP_NONE;
@@ -395,26 +666,35 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
   if (counters) ct.newv += m;
   if (c.nv - k + m > kBigV) return CLIP_OVERFLOW;
   __syncwarp();
-  // keep the inside vertices (in-place compaction), then append the new ones
+  // keep the inside vertices (in-place compaction), then append the new ones;
+  // a row is stored at or below the index it was loaded from, and every load
+  // of a step precedes its stores, so no row is overwritten before it is read
   int kept = 0;
-  for (int base = 0; base < c.nv; base += 32) {
-    int i = base + (int)lane;
-    bool keep = false;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint64_t T = 0;
-    if (i < c.nv) {
-      T = A.vt[i];
-      keep = (T & kBigOut) == 0;
-      if (keep) v = A.vp[i];
+  for (int base = 0; base < c.nv; base += 128) {
+    float4 v[4];
+    uint64_t T[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int i = base + 32 * u + (int)lane;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      T[u] = kBigOut;
+      if (i < c.nv) {
+        T[u] = A.vt[i];
+        v[u] = A.vp[i];
+      }
     }
-    uint32_t km = __ballot_sync(FULL, keep);
-    int dst = kept + __popc(km & lt);
     __syncwarp();
-    if (keep) {
-      A.vp[dst] = v;
-      A.vt[dst] = T;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const bool keep = (T[u] & kBigOut) == 0;
+      const uint32_t km = __ballot_sync(FULL, keep);
+      const int dst = kept + __popc(km & lt);
+      if (keep) {
+        A.vp[dst] = v[u];
+        A.vt[dst] = T[u];
+      }
+      kept += __popc(km);
     }
-    kept += __popc(km);
     __syncwarp();
   }
   for (int t = (int)lane; t < m; t += 32) {
@@ -423,16 +703,27 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
   }
   c.nv = kept + m;
   __syncwarp();
+  if (c.nv > kSortMin) big_sort_vertices(c, A);
+  big_chunk_boxes(c, A);
   return CLIP_DONE;
 }
 
 // ---------------------------------------------------------------- queue
-__device__ inline bool big_push(BigCell& c, const BigArena& A, float lb, int ref, int occ) {
+__device__ inline bool big_push(BigCell& c, const BigArena& A, float lb, float key, int traversal, int ref, int occ) {
   if (c.qn >= kBigQ) return false;
   if (lane_id() == 0) {
-    A.qlb[c.qn] = lb;
-    A.qref[c.qn] = ref;
-    A.qocc[c.qn] = occ | (c.seq << 8);
+    // sift up from the new leaf
+    const uint32_t k = traversal == 0 ? f2o(key) : 0xfffffffeu - (uint32_t)c.seq;
+    const int4 e = make_int4((int)k, __float_as_int(lb), ref, occ | (c.seq << 8));
+    int i = c.qn;
+    while (i > 0) {
+      const int p = (i - 1) >> 5;
+      const int4 pe = A.q[p];
+      if ((uint32_t)pe.x <= k) break;
+      A.q[i] = pe;
+      i = p;
+    }
+    A.q[i] = e;
   }
   c.qn++;
   c.seq++;
@@ -440,58 +731,41 @@ __device__ inline bool big_push(BigCell& c, const BigArena& A, float lb, int ref
   return true;
 }
 
-// Pop the best entry still valid under the current bounds; entries that
-// fail the re-test are dropped, the popped slot takes the last entry
-// (App. A.5).
-__device__ inline bool big_pop(BigCell& c, const BigArena& A, int cull_mode, int traversal, int& ref) {
-  const unsigned lane = lane_id(), lt = lanemask_lt();
-  int live = 0;
-  uint32_t bestk = 0xffffffffu;
-  int besti = 0x7fffffff;
-  for (int base = 0; base < c.qn; base += 32) {
-    int i = base + (int)lane;
-    bool ok = false;
-    float lb = 0.f;
-    int rf = 0, oc = 0;
-    uint32_t key = 0xffffffffu;
-    if (i < c.qn) {
-      lb = A.qlb[i];
-      rf = A.qref[i];
-      oc = A.qocc[i];
-      float R = A.rtab[oc & 63];
-      ok = cull_mode == 2 || !(lb > R * (1.0f + kCullPad));
-      key = traversal == 0 ? f2o(lb - R) : (0xfffffffeu - (uint32_t)(oc >> 8));
+// Pop the entry of least key (the key is fixed when the entry is pushed);
+// an entry that fails the re-test under the current bounds is dropped and
+// the next one taken. The heap is 32-ary, so each level of the sift-down is
+// one coalesced load of the 32 children and a warp minimum.
+__device__ inline bool big_pop(BigCell& c, const BigArena& A, int cull_mode, int& ref) {
+  const unsigned lane = lane_id();
+  while (c.qn > 0) {
+    const int4 top = A.q[0];
+    c.qn--;
+    const int4 last = A.q[c.qn];
+    int i = 0;
+    while (true) {
+      const int c0 = 32 * i + 1;
+      if (c0 >= c.qn) break;
+      const int j = c0 + (int)lane;
+      int4 ch = make_int4(-1, 0, 0, 0);
+      if (j < c.qn) ch = A.q[j];
+      const uint32_t mn = __reduce_min_sync(FULL, (uint32_t)ch.x);
+      if (mn >= (uint32_t)last.x) break;
+      const int src = __ffs(__ballot_sync(FULL, j < c.qn && (uint32_t)ch.x == mn)) - 1;
+      __syncwarp();
+      if ((int)lane == src) A.q[i] = ch;
+      i = c0 + src;
     }
-    uint32_t km = __ballot_sync(FULL, ok);
-    int dst = live + __popc(km & lt);
     __syncwarp();
-    if (ok) {
-      A.qlb[dst] = lb;
-      A.qref[dst] = rf;
-      A.qocc[dst] = oc;
-      if (key < bestk) {
-        bestk = key;
-        besti = dst;
-      }
+    if (lane == 0 && c.qn > 0) A.q[i] = last;
+    __syncwarp();
+    const float lb = __int_as_float(top.y);
+    const float R = A.rtab[top.w & 63];
+    if (cull_mode == 2 || !(lb > R * (1.0f + kCullPad))) {
+      ref = top.z;
+      return true;
     }
-    live += __popc(km);
-    __syncwarp();
   }
-  c.qn = live;
-  uint32_t mn = __reduce_min_sync(FULL, bestk);
-  if (mn == 0xffffffffu || live == 0) return false;
-  int idx = (int)__reduce_min_sync(FULL, bestk == mn ? (uint32_t)besti : 0x7fffffffu);
-  ref = A.qref[idx];
-  __syncwarp();
-  if (lane == 0) {
-    int last = c.qn - 1;
-    A.qlb[idx] = A.qlb[last];
-    A.qref[idx] = A.qref[last];
-    A.qocc[idx] = A.qocc[last];
-  }
-  c.qn--;
-  __syncwarp();
-  return true;
+  return false;
 }
 
 // Fill the pair hash with every vertex's three directed pairs -> vertex.

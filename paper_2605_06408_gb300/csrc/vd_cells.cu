@@ -438,6 +438,20 @@ __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig
   }
   uint32_t km = __ballot_sync(FULL, keep);
   if (counters) ct.cand += __popc(km);
+  if (km) {
+    // test all survivors against the polytope at once; those that cut
+    // nothing are done
+    const int rank = __popc(km & lanemask_lt());
+    if (keep) {
+      A.hs[rank] = make_float4(H.nx, H.ny, H.nz, H.b);
+      A.hse[rank] = H.e;
+    }
+    __syncwarp();
+    const uint32_t cm = big_filter(c, A, __popc(km), ct, counters);
+    keep = keep && ((cm >> rank) & 1u);
+    km = __ballot_sync(FULL, keep);
+    __syncwarp();
+  }
   while (km) {
     uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
     uint32_t mn = __reduce_min_sync(FULL, key);
@@ -641,7 +655,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
           float flb = __shfl_sync(FULL, lb, fsrc);
           int focc = __shfl_sync(FULL, occ, fsrc);
           cur = near0 ? r0 : r1;
-          if (!big_push(c, A, flb, near0 ? r1 : r0, focc)) {
+          if (!big_push(c, A, flb, near0 ? key1 : key0, trav, near0 ? r1 : r0, focc)) {
             overflow = true;
             break;
           }
@@ -655,7 +669,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
       }
       if (have) continue;
     }
-    if (!big_pop(c, A, cull, trav, cur)) break;
+    if (!big_pop(c, A, cull, cur)) break;
     have = true;
   }
   if (overflow) return false;
@@ -789,7 +803,10 @@ cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, cons
   if (err != cudaSuccess) return err;
   between();
   // cells that overflowed the register-resident capacity
-  big_cells_kernel<<<num_sms, 32 * kBigWarpsPerBlock, 0, s>>>(c);
+  const size_t big_smem = kBigSmemPerWarp * kBigWarpsPerBlock;
+  err = cudaFuncSetAttribute(big_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+  if (err != cudaSuccess) return err;
+  big_cells_kernel<<<num_sms, 32 * kBigWarpsPerBlock, big_smem, s>>>(c);
   return cudaGetLastError();
 }
 
