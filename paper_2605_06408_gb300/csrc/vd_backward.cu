@@ -300,6 +300,7 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
       if (rc == CLIP_EMPTY) return true;
     }
   }
+  big_compact(c, A);
   big_mark_planes(c, A);
   const uint32_t hmask = big_hash_vertices(c, A);
   float sx = 0.f, sy = 0.f, sz = 0.f;

@@ -16,10 +16,19 @@
 // error bound), rebuilt after every clip, and the read-only first pass tests
 // a chunk's vertices only when the plane reaches the chunk's box. To keep
 // the chunks compact, the vertex array of a large polytope is re-sorted after
-// every clip by the cube-map cell of its direction from the polytope's box
-// centre (6 faces x 8 x 8 cells, Morton order within a face), so a chunk is a
-// small patch of the surface and a plane that passes close to the polytope
-// reaches the boxes of only a few patches.
+// clips by the cube-map cell of its direction from the polytope's box centre
+// (6 faces x 8 x 8 cells, Morton order within a face), so a chunk is a small
+// patch of the surface and a plane that passes close to the polytope reaches
+// the boxes of only a few patches.
+//
+// Vertex slots are not compacted after a clip: the new vertices of a clip
+// take the slots of the vertices it removed (which lie where the new ones
+// appear), extra ones come from a stack of free slots or the end of the
+// array, and unused slots become dead (NaN position, which every sign test
+// reads as inside and every box ignores). A clip therefore reads and writes
+// only the chunks its plane reaches and refreshes only their boxes. The
+// array is re-sorted, dropping dead slots, once the vertices placed outside
+// their neighbours' chunks since the last sort pass 1/16 of the polytope.
 #pragma once
 
 #include "vd_clip.cuh"
@@ -32,8 +41,8 @@ constexpr int kBigQ = 8192;    // queue entries
 constexpr int kBigH = 65536;   // pair-hash slots (power of two)
 constexpr int kBigC = kBigV / 32;  // chunk boxes
 constexpr int kBigGc = (kBigP * 85) / 100;
-constexpr uint64_t kBigOut = 1ull << 63;
 constexpr uint64_t kTriMask = 0x0000ffffffffffffull;
+constexpr uint64_t kBigDead = kTriMask;  // triplet of a dead slot
 constexpr uint32_t kHashEmpty = 0xffffffffu;
 
 struct BigArena {
@@ -52,10 +61,15 @@ struct BigArena {
   float* acc;
   float* rtab;  // [64] cell radius per occupied-octant mask
   float4* cb;   // [2 kBigC] chunk q: cb[2q] = (lo, max error), cb[2q+1] = (hi, 0)
+  int* fs;      // [kBigV] free-slot stack
+  int* os;      // [kBigV] slots of the vertices a clip removes
   // shared memory of the warp
   float4* hs;      // [32] staged candidate planes (n, b)
   float* hse;      // [32] their error bounds
+  int* hid;        // [32] their sites
+  float* hord;     // [32] their clip order key (plane offset)
   uint32_t* hist;  // [kDirBins] direction-bin counts / cursors
+  uint32_t* cdirty;  // [kBigC / 32] chunks whose box is stale
 };
 
 constexpr int kDirBins = 6 * 64;
@@ -63,7 +77,7 @@ constexpr int kDirBins = 6 * 64;
 constexpr int kSortMin = 128;
 
 // Shared memory per warp of the large-cell kernels.
-constexpr size_t kBigSmemPerWarp = 32 * 16 + 32 * 4 + kDirBins * 4;
+constexpr size_t kBigSmemPerWarp = 32 * 16 + 3 * 32 * 4 + kDirBins * 4 + kBigC / 8;
 
 __host__ __device__ inline size_t big_arena_bytes() {
   size_t b = 64 * 4;
@@ -73,6 +87,7 @@ __host__ __device__ inline size_t big_arena_bytes() {
   b += (size_t)kBigH * 8;
   b += (size_t)kBigP * 10 * 4;
   b += 64 * 4 + (size_t)kBigC * 32;
+  b += (size_t)kBigV * 8;
   return (b + 255) & ~(size_t)255;
 }
 
@@ -108,11 +123,18 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   A.rtab = (float*)p;
   p += 64 * 4;
   A.cb = (float4*)p;
+  p += (size_t)kBigC * 32;
+  A.fs = (int*)p;
+  p += (size_t)kBigV * 4;
+  A.os = (int*)p;
   extern __shared__ __align__(16) char big_smem[];
   char* w = big_smem + (size_t)(threadIdx.x >> 5) * kBigSmemPerWarp;
   A.hs = (float4*)w;
   A.hse = (float*)(w + 32 * 16);
-  A.hist = (uint32_t*)(w + 32 * 16 + 32 * 4);
+  A.hid = (int*)(w + 32 * 16 + 32 * 4);
+  A.hord = (float*)(w + 32 * 16 + 2 * 32 * 4);
+  A.hist = (uint32_t*)(w + 32 * 16 + 3 * 32 * 4);
+  A.cdirty = (uint32_t*)(w + 32 * 16 + 3 * 32 * 4 + kDirBins * 4);
   return A;
 }
 
@@ -121,9 +143,16 @@ struct BigCell {
   float lo[3], hi[3];
   float alo[3], ahi[3];
   float sc[3], srad;
-  int nv, npl, qn, seq;
+  int nv;        // vertex slots in use (live and dead)
+  int nlive;     // live vertices
+  int nfree;     // dead slots on the free-slot stack
+  int unsorted;  // vertices placed away from their clip's chunks since the last sort
+  int npl, qn, seq;
+  int nst;  // candidate planes staged in A.hs for the next filter
   bool dirty;
 };
+
+__device__ __forceinline__ bool bdead(uint64_t T) { return (T & kTriMask) == kTriMask; }
 
 // ---------------------------------------------------------------- triplets
 __device__ __forceinline__ uint64_t btri(uint32_t a, uint32_t b, uint32_t c) {
@@ -221,15 +250,16 @@ __device__ __forceinline__ uint32_t dir_bin(float dx, float dy, float dz) {
   return f * 64u + mo;
 }
 
-// Stable counting sort of the vertex array by direction bin about the box
-// centre (c.sc), through the staging arrays nvp / nvt.
-__device__ inline void big_sort_vertices(const BigCell& c, const BigArena& A) {
+// Stable counting sort of the live vertices by direction bin about the box
+// centre (c.sc), through the staging arrays nvp / nvt; dead slots are
+// dropped (bins == 1: compaction only, order kept).
+__device__ inline void big_sort_vertices(BigCell& c, const BigArena& A, bool bins = true) {
   const unsigned lane = lane_id(), lt = lanemask_lt();
   for (int b = (int)lane; b < kDirBins; b += 32) A.hist[b] = 0;
   __syncwarp();
   for (int i = (int)lane; i < c.nv; i += 32) {
     const float4 v = A.vp[i];
-    atomicAdd(&A.hist[dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2])], 1u);
+    if (!bdead(A.vt[i])) atomicAdd(&A.hist[bins ? dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2]) : 0u], 1u);
   }
   __syncwarp();
   // exclusive scan: lane l owns bins [12 l, 12 l + 12)
@@ -265,18 +295,21 @@ __device__ inline void big_sort_vertices(const BigCell& c, const BigArena& A) {
     if (in) {
       v = A.vp[i];
       T = A.vt[i];
-      b = dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2]);
+      if (!bdead(T)) b = bins ? dir_bin(v.x - c.sc[0], v.y - c.sc[1], v.z - c.sc[2]) : 0u;
     }
     const uint32_t peers = __match_any_sync(FULL, b);
-    const int pos = in ? (int)A.hist[b] + __popc(peers & lt) : 0;
+    const int pos = b != 0xffffffffu ? (int)A.hist[b] + __popc(peers & lt) : 0;
     __syncwarp();
-    if (in) {
+    if (b != 0xffffffffu) {
       A.nvp[pos] = v;
       A.nvt[pos] = T;
       if ((peers & lt) == 0) A.hist[b] += __popc(peers);
     }
     __syncwarp();
   }
+  c.nv = c.nlive;
+  c.nfree = 0;
+  c.unsorted = 0;
   for (int i = (int)lane; i < c.nv; i += 32) {
     A.vp[i] = A.nvp[i];
     A.vt[i] = A.nvt[i];
@@ -284,11 +317,16 @@ __device__ inline void big_sort_vertices(const BigCell& c, const BigArena& A) {
   __syncwarp();
 }
 
+// Drop dead slots (order kept): the array is dense afterwards, as the
+// volume and gradient passes expect.
+__device__ inline void big_compact(BigCell& c, const BigArena& A) {
+  if (c.nlive != c.nv) big_sort_vertices(c, A, false);
+}
+
 // Chunk boxes of the current vertex array (exact min / max of the stored
 // FP32 positions).
-__device__ inline void big_chunk_boxes(const BigCell& c, const BigArena& A) {
-  const int nch = (c.nv + 31) >> 5;
-  for (int q = (int)lane_id(); q < nch; q += 32) {
+__device__ inline void big_chunk_box(const BigCell& c, const BigArena& A, int q) {
+  {
     float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, em = 0.0f;
     const int i1 = min(c.nv, 32 * q + 32);
 #pragma unroll 8
@@ -304,6 +342,26 @@ __device__ inline void big_chunk_boxes(const BigCell& c, const BigArena& A) {
     }
     A.cb[2 * q] = make_float4(lx, ly, lz, em);
     A.cb[2 * q + 1] = make_float4(hx, hy, hz, 0.0f);
+  }
+}
+
+__device__ inline void big_chunk_boxes(const BigCell& c, const BigArena& A) {
+  const int nch = (c.nv + 31) >> 5;
+  for (int q = (int)lane_id(); q < nch; q += 32) big_chunk_box(c, A, q);
+  for (int w = (int)lane_id(); w < kBigC / 32; w += 32) A.cdirty[w] = 0;
+  __syncwarp();
+}
+
+// Refresh the boxes of the chunks marked in A.cdirty.
+__device__ inline void big_dirty_boxes(const BigCell& c, const BigArena& A) {
+  const int nch = (c.nv + 31) >> 5;
+  for (int w = 0; w < (nch + 31) >> 5; w++) {
+    const uint32_t bits = A.cdirty[w];
+    if (bits == 0) continue;
+    const int q = 32 * w + (int)lane_id();
+    if ((bits >> lane_id()) & 1u) big_chunk_box(c, A, q);
+    __syncwarp();
+    if (lane_id() == 0) A.cdirty[w] = 0;
   }
   __syncwarp();
 }
@@ -326,12 +384,40 @@ __device__ __forceinline__ bool chunk_may_cut(const PlaneT<float>& H, float4 lo,
 // Polytopes of at most this many chunks are scanned without the box stage.
 constexpr int kBoxStage = 2;
 
-// Leaf-batch filter: which of the k <= 32 planes staged in A.hs / A.hse may
+// Batch filter: which of the k <= 32 planes staged in A.hs / A.hse may
 // cut the polytope (some vertex outside or ambiguous)? Bit t of the result
 // stands for plane t. Each vertex chunk is loaded once for all planes whose
 // test reaches its box. A plane that leaves every vertex certainly inside
 // also leaves every later (clipped, smaller) polytope of the cell inside, so
 // the caller drops it for good.
+// The staged planes of mask m, four per step so that their shared-memory
+// loads and tests overlap; f(t, H) is called for each.
+template <typename F>
+__device__ __forceinline__ void for_staged_planes(const BigArena& A, uint32_t m, F f) {
+  while (m) {
+    int t[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      t[u] = m ? __ffs(m) - 1 : -1;
+      m &= m ? m - 1 : 0u;
+    }
+    PlaneT<float> H[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int tt = t[u] < 0 ? t[0] : t[u];
+      const float4 h = A.hs[tt];
+      H[u].nx = h.x;
+      H[u].ny = h.y;
+      H[u].nz = h.z;
+      H[u].b = h.w;
+      H[u].e = A.hse[tt];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+      if (t[u] >= 0) f(t[u], H[u]);
+  }
+}
+
 __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k, Counters& ct, bool counters) {
   const unsigned lane = lane_id();
   uint32_t open = k >= 32 ? FULL : ((1u << k) - 1u);
@@ -346,17 +432,9 @@ __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k
         fl = open;
       } else {
         const float4 lo = A.cb[2 * q], hi = A.cb[2 * q + 1];
-        for (uint32_t m = open; m; m &= m - 1) {
-          const int t = __ffs(m) - 1;
-          const float4 h = A.hs[t];
-          PlaneT<float> H;
-          H.nx = h.x;
-          H.ny = h.y;
-          H.nz = h.z;
-          H.b = h.w;
-          H.e = A.hse[t];
+        for_staged_planes(A, open, [&](int t, const PlaneT<float>& H) {
           if (chunk_may_cut(H, lo, hi)) fl |= 1u << t;
-        }
+        });
       }
     }
     uint32_t U = __ballot_sync(FULL, fl != 0);
@@ -380,18 +458,11 @@ __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k
       for (int u = 0; u < 4; u++) {
         const int i = 32 * (cbase + (qs[u] < 0 ? 0 : qs[u])) + (int)lane;
         if (i < c.nv) {
-          for (uint32_t m = pms[u]; m; m &= m - 1) {
-            const int t = __ffs(m) - 1;
-            const float4 h = A.hs[t];
-            PlaneT<float> H;
-            H.nx = h.x;
-            H.ny = h.y;
-            H.nz = h.z;
-            H.b = h.w;
-            H.e = A.hse[t];
-            const float s = side<float>(H, v[u].x, v[u].y, v[u].z);
-            if (s > 0.0f || ambiguous<float>(s, v[u].w, H.e)) outm |= 1u << t;
-          }
+          const float4 w = v[u];
+          for_staged_planes(A, pms[u], [&](int t, const PlaneT<float>& H) {
+            const float s = side<float>(H, w.x, w.y, w.z);
+            if (s > 0.0f || ambiguous<float>(s, w.w, H.e)) outm |= 1u << t;
+          });
         }
         tested += 32 * __popc(pms[u]);
       }
@@ -456,6 +527,10 @@ __device__ inline void big_init(BigCell& c, const BigArena& A, int cull_mode) {
     A.vt[lane] = btri(a, b, d);
   }
   c.nv = 8;
+  c.nlive = 8;
+  c.nfree = 0;
+  c.unsorted = 0;
+  c.nst = 0;
   c.npl = 6;
   c.qn = 0;
   c.seq = 0;
@@ -471,6 +546,7 @@ __device__ inline void big_mark_planes(const BigCell& c, const BigArena& A) {
   __syncwarp();
   for (int i = (int)lane_id(); i < c.nv; i += 32) {
     uint64_t T = A.vt[i];
+    if (bdead(T)) continue;
 #pragma unroll
     for (int f = 0; f < 3; f++) A.flag[bfield(T, f)] = 1;
   }
@@ -508,7 +584,7 @@ __device__ inline void big_gc(BigCell& c, const BigArena& A) {
   }
   for (int i = (int)lane; i < c.nv; i += 32) {
     uint64_t T = A.vt[i];
-    A.vt[i] = btri(A.flag[bfield(T, 0)], A.flag[bfield(T, 1)], A.flag[bfield(T, 2)]);
+    if (!bdead(T)) A.vt[i] = btri(A.flag[bfield(T, 0)], A.flag[bfield(T, 1)], A.flag[bfield(T, 2)]);
   }
   c.npl = alive;
   __syncwarp();
@@ -571,45 +647,57 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
     if (counters) ct.vtests += tested;
     if (!any) return CLIP_NONE;
   }
-  // classify; mark outside vertices and list their triplets (four rows of
-  // loads in flight per step)
+  // classify the vertices of the chunks the plane reaches; list the outside
+  // ones' triplets (otri) and slots (os)
   int k = 0;
-  for (int base = 0; base < c.nv; base += 128) {
-    float4 v[4];
-    uint64_t T[4];
+  {
+    const int nch = (c.nv + 31) >> 5;
+    for (int cbase = 0; cbase < nch; cbase += 32) {
+      const int q = cbase + (int)lane;
+      bool f = q < nch;
+      if (f && nch > kBoxStage) f = chunk_may_cut(H, A.cb[2 * q], A.cb[2 * q + 1]);
+      uint32_t fm = __ballot_sync(FULL, f);
+      while (fm) {
+        int qs[4];
+        float4 v[4];
+        uint64_t T[4];
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int i = base + 32 * u + (int)lane;
-      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      T[u] = 0;
-      if (i < c.nv) {
-        v[u] = A.vp[i];
-        T[u] = A.vt[i];
-      }
-    }
+        for (int u = 0; u < 4; u++) {
+          qs[u] = fm ? cbase + __ffs(fm) - 1 : -1;
+          fm &= fm ? fm - 1 : 0u;
+          const int i = 32 * qs[u] + (int)lane;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          T[u] = kBigDead;
+          if (qs[u] >= 0 && i < c.nv) {
+            v[u] = A.vp[i];
+            T[u] = A.vt[i];
+          }
+        }
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int i = base + 32 * u + (int)lane;
-      bool out = false;
-      if (i < c.nv) {
-        float s = side<float>(H, v[u].x, v[u].y, v[u].z);
-        out = s > 0.0f;
-        if (ambiguous<float>(s, v[u].w, H.e)) {
-          ct.fp64++;
-          out = big_resolve64(A, T[u], hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
+        for (int u = 0; u < 4; u++) {
+          const int i = 32 * qs[u] + (int)lane;
+          bool out = false;
+          if (!bdead(T[u])) {
+            float s = side<float>(H, v[u].x, v[u].y, v[u].z);
+            out = s > 0.0f;
+            if (ambiguous<float>(s, v[u].w, H.e)) {
+              ct.fp64++;
+              out = big_resolve64(A, T[u], hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
+            }
+          }
+          uint32_t m = __ballot_sync(FULL, out);
+          if (out) {
+            A.otri[k + __popc(m & lt)] = T[u];
+            A.os[k + __popc(m & lt)] = i;
+          }
+          k += __popc(m);
         }
       }
-      uint32_t m = __ballot_sync(FULL, out);
-      if (out) {
-        A.otri[k + __popc(m & lt)] = T[u];
-        A.vt[i] = T[u] | kBigOut;
-      }
-      k += __popc(m);
     }
   }
   __syncwarp();
   if (k == 0) return CLIP_NONE;
-  if (k == c.nv) return CLIP_EMPTY;
+  if (k == c.nlive) return CLIP_EMPTY;
   const int h = c.npl++;
   if (lane == 0) {
     A.pl[h] = make_float4(H.nx, H.ny, H.nz, H.b);
@@ -664,47 +752,45 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
     m += __popc(nm);
   }
   if (counters) ct.newv += m;
-  if (c.nv - k + m > kBigV) return CLIP_OVERFLOW;
+  if (m > k + c.nfree + (kBigV - c.nv)) return CLIP_OVERFLOW;
   __syncwarp();
-  // keep the inside vertices (in-place compaction), then append the new ones;
-  // a row is stored at or below the index it was loaded from, and every load
-  // of a step precedes its stores, so no row is overwritten before it is read
-  int kept = 0;
-  for (int base = 0; base < c.nv; base += 128) {
-    float4 v[4];
-    uint64_t T[4];
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const int i = base + 32 * u + (int)lane;
-      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      T[u] = kBigOut;
-      if (i < c.nv) {
-        T[u] = A.vt[i];
-        v[u] = A.vp[i];
-      }
+  // new vertex t takes the slot of removed vertex t, then free slots, then
+  // slots at the end; removed slots left over become dead and free
+  const int from_free = min(max(m - k, 0), c.nfree);
+  for (int t = (int)lane; t < max(m, k); t += 32) {
+    int slot;
+    if (t < k)
+      slot = A.os[t];
+    else if (t - k < from_free)
+      slot = A.fs[c.nfree - 1 - (t - k)];
+    else
+      slot = c.nv + (t - k - from_free);
+    if (t < m) {
+      A.vp[slot] = A.nvp[t];
+      A.vt[slot] = A.nvt[t];
+    } else {
+      A.vp[slot] = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000), __int_as_float(0x7fc00000), 0.0f);
+      A.vt[slot] = kBigDead;
     }
-    __syncwarp();
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const bool keep = (T[u] & kBigOut) == 0;
-      const uint32_t km = __ballot_sync(FULL, keep);
-      const int dst = kept + __popc(km & lt);
-      if (keep) {
-        A.vp[dst] = v[u];
-        A.vt[dst] = T[u];
-      }
-      kept += __popc(km);
-    }
-    __syncwarp();
+    atomicOr(&A.cdirty[slot >> 10], 1u << ((slot >> 5) & 31));
   }
-  for (int t = (int)lane; t < m; t += 32) {
-    A.vp[kept + t] = A.nvp[t];
-    A.vt[kept + t] = A.nvt[t];
-  }
-  c.nv = kept + m;
   __syncwarp();
-  if (c.nv > kSortMin) big_sort_vertices(c, A);
-  big_chunk_boxes(c, A);
+  if (m < k) {
+    for (int t = m + (int)lane; t < k; t += 32) A.fs[c.nfree + (t - m)] = A.os[t];
+    c.nfree += k - m;
+  } else {
+    c.nfree -= from_free;
+    c.nv += m - k - from_free;
+    c.unsorted += m - k;
+  }
+  c.nlive += m - k;
+  __syncwarp();
+  if (c.nlive > kSortMin && c.unsorted > max(64, c.nlive >> 4)) {
+    big_sort_vertices(c, A);
+    big_chunk_boxes(c, A);
+  } else {
+    big_dirty_boxes(c, A);
+  }
   return CLIP_DONE;
 }
 

@@ -405,6 +405,44 @@ __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
 
 // ---------------------------------------------------------------- large cells
 
+// Filter the staged candidate planes against the polytope; clip by those
+// that may cut, nearest plane first. Returns CLIP_EMPTY / CLIP_OVERFLOW, or
+// CLIP_NONE (c.dirty set if the polytope changed).
+__device__ int big_flush(BigCell& c, const BigArena& A, const float4* __restrict__ sites, Counters& ct,
+                         bool counters) {
+  const unsigned lane = lane_id();
+  const int k = c.nst;
+  if (k == 0) return CLIP_NONE;
+  c.nst = 0;
+  const uint32_t cm = big_filter(c, A, k, ct, counters);
+  bool keep = (int)lane < k && ((cm >> lane) & 1u);
+  const float dkey = keep ? A.hord[lane] : INFINITY;
+  uint32_t km = __ballot_sync(FULL, keep);
+  while (km) {
+    const uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
+    const uint32_t mn = __reduce_min_sync(FULL, key);
+    const int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
+    const float4 h = A.hs[src];
+    PlaneT<float> Hb;
+    Hb.nx = h.x;
+    Hb.ny = h.y;
+    Hb.nz = h.z;
+    Hb.b = h.w;
+    Hb.e = A.hse[src];
+    const int hj = A.hid[src];
+    if ((int)lane == src) keep = false;
+    km &= ~(1u << src);
+    const int rc = big_clip(c, A, Hb, hj, sites, ct, counters);
+    if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW) return rc;
+    if (rc == CLIP_DONE) {
+      c.dirty = true;
+      if (counters) ct.clips++;
+    }
+  }
+  __syncwarp();
+  return CLIP_NONE;
+}
+
 __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig_i, const CellBuffers& P,
                         Counters& ct, int skip0, int skip1) {
   const unsigned lane = lane_id();
@@ -438,39 +476,22 @@ __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig
   }
   uint32_t km = __ballot_sync(FULL, keep);
   if (counters) ct.cand += __popc(km);
-  if (km) {
-    // test all survivors against the polytope at once; those that cut
-    // nothing are done
-    const int rank = __popc(km & lanemask_lt());
-    if (keep) {
-      A.hs[rank] = make_float4(H.nx, H.ny, H.nz, H.b);
-      A.hse[rank] = H.e;
-    }
-    __syncwarp();
-    const uint32_t cm = big_filter(c, A, __popc(km), ct, counters);
-    keep = keep && ((cm >> rank) & 1u);
-    km = __ballot_sync(FULL, keep);
-    __syncwarp();
+  if (!km) return CLIP_NONE;
+  // stage the survivors; the staged planes of several leaves are filtered
+  // together (a bound computed before their clips is only looser)
+  if (c.nst + __popc(km) > 32) {
+    const int rc = big_flush(c, A, P.sites, ct, counters);
+    if (rc != CLIP_NONE) return rc;
   }
-  while (km) {
-    uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
-    uint32_t mn = __reduce_min_sync(FULL, key);
-    int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
-    PlaneT<float> Hb;
-    Hb.nx = __shfl_sync(FULL, H.nx, src);
-    Hb.ny = __shfl_sync(FULL, H.ny, src);
-    Hb.nz = __shfl_sync(FULL, H.nz, src);
-    Hb.b = __shfl_sync(FULL, H.b, src);
-    Hb.e = __shfl_sync(FULL, H.e, src);
-    if ((int)lane == src) keep = false;
-    km &= ~(1u << src);
-    int rc = big_clip(c, A, Hb, first + src, P.sites, ct, counters);
-    if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW) return rc;
-    if (rc == CLIP_DONE) {
-      c.dirty = true;
-      if (counters) ct.clips++;
-    }
+  const int slot = c.nst + __popc(km & lanemask_lt());
+  if (keep) {
+    A.hs[slot] = make_float4(H.nx, H.ny, H.nz, H.b);
+    A.hse[slot] = H.e;
+    A.hid[slot] = j;
+    A.hord[slot] = dkey;
   }
+  c.nst += __popc(km);
+  __syncwarp();
   return CLIP_NONE;
 }
 
@@ -605,6 +626,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     skip0 = max(lo, min(si - 16, hi - 32));
     skip1 = min(hi, skip0 + 32);
     int rc = big_leaf(c, A, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, ct, 0, 0);
+    if (rc == CLIP_NONE) rc = big_flush(c, A, P.sites, ct, counters);
     if (rc == CLIP_EMPTY) empty = true;
     if (rc == CLIP_OVERFLOW) return false;
     if (c.dirty) {
@@ -672,6 +694,15 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     if (!big_pop(c, A, cull, cur)) break;
     have = true;
   }
+  if (!empty && !overflow) {
+    const int rc = big_flush(c, A, P.sites, ct, counters);
+    if (rc == CLIP_EMPTY) empty = true;
+    if (rc == CLIP_OVERFLOW) overflow = true;
+    if (c.dirty) {
+      big_aabb(c, A, cull);
+      c.dirty = false;
+    }
+  }
   if (overflow) return false;
   if (empty) {
     if (lane == 0) {
@@ -684,6 +715,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     empties++;
     return true;
   }
+  big_compact(c, A);
   // neighbours: site planes that carry a face, sorted, into the pool
   big_mark_planes(c, A);
   int* list = reinterpret_cast<int*>(A.otri);
