@@ -76,8 +76,8 @@ typedef struct {
                         /*   may be NULL                                           */
 } vd_out;
 
-/* Tuning knobs. vd_default_config fills the defaults; the autotuner of the
- * Python layer overrides them per workload. */
+/* Tuning knobs. vd_default_config fills the defaults; vd_autotune picks them
+ * per workload by timing candidate configurations. */
 typedef struct {
   int32_t leaf_size;       /* LBVH leaf size (1..32); default 16                     */
   int32_t verts_per_lane;  /* polytope capacity per cell = 32 * this (2 or 4)        */
@@ -91,7 +91,13 @@ typedef struct {
   int32_t timing;          /* 1: record CUDA events around each phase (vd_get_timings)*/
   int32_t warm_start;      /* 1: clip each cell first with its 32 Morton-order       */
                            /*    neighbours (App. A.6 warm start, without KNN);     */
-                           /*    default 0 (best-first reaches that leaf first)     */
+                           /*    default 0 (best-first reaches that leaf first);    */
+                           /*    warp-per-cell form only                            */
+  int32_t cell_mode;       /* 0: one warp per cell, polytope in registers (default);*/
+                           /* 1: one thread per cell, polytope in per-thread memory */
+                           /*    (the paper's mapping, App. A.3: 64 vertices, 48    */
+                           /*    planes, 48 queue entries per cell); cells beyond   */
+                           /*    either capacity go to the large-cell pass          */
 } vd_config;
 
 /* Device-side results of the last call, read back by vd_get_status. */
@@ -217,6 +223,34 @@ int vd_get_status(vd_ctx* ctx, vd_status* st);
 
 /* Static string for a VD_* code (never NULL). */
 const char* vd_error_string(int code);
+
+/* ---- autotuner (a project addition: the paper has no tuner; its kernel
+ * capacities are fixed per build) ------------------------------------------
+ *
+ * vd_autotune / vd_autotune_batched time candidate configurations of
+ * vd_build / vd_build_batched on the caller's input and keep the fastest in
+ * ctx (returned in *best when best != NULL). Coordinate descent from the
+ * context's configuration over: cell_mode (warp or thread per cell),
+ * verts_per_lane (polytope capacity), queue_per_lane (queue depth),
+ * leaf_size, warps_per_block and warm_start; each trial is one warm-up and
+ * two timed builds (CUDA events), a change is kept if >= 2% faster, at most
+ * max_trials trials (<= 0: 16). cull_mode, traversal, counters and timing
+ * stay the caller's. The result is cached in ctx per (floor(log2 n), any
+ * set weighted, set-count class); a later call with the same key returns
+ * the cached configuration without trials unless flags has VD_TUNE_FORCE.
+ *
+ * Synchronises the host (it reads timings); not capturable into a CUDA
+ * graph: tune first, then capture vd_build / vd_build_batched. Allocates and
+ * frees its own scratch outputs (about 4 (28 n) bytes) and leaves no forward
+ * state (vd_backward needs a new vd_build). Errors: VD_ERR_INVALID_ARG as
+ * vd_build; VD_ERR_CUDA; VD_ERR_CELL_OVERFLOW if no configuration could
+ * build every cell (ctx keeps its configuration). */
+#define VD_TUNE_FORCE 1
+int vd_autotune(vd_ctx* ctx, const float* sites_xyz, const float* weights, int64_t n, vd_box bbox,
+                int32_t max_trials, int32_t flags, vd_config* best, void* stream);
+int vd_autotune_batched(vd_ctx* ctx, const float* sites_xyz, const float* weights, const int64_t* set_offsets,
+                        const vd_box* boxes, const uint8_t* weighted, int32_t nsets, int32_t max_trials,
+                        int32_t flags, vd_config* best, void* stream);
 
 /* ------------------------------------------------- allocation-free variant */
 

@@ -5,7 +5,10 @@
 // workspace growth (cudaMalloc) and vd_get_status.
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <new>
+#include <tuple>
 
 #include "vd_big.cuh"
 
@@ -89,6 +92,8 @@ struct vd_ctx {
   bool ev_valid = false;
   bool ev_backward = false;
   int launches = 0;
+  // autotuner: best configuration per (log2 n, weighted, set count)
+  std::map<std::tuple<int, int, int>, vd_config> tuned;
 };
 
 // events 0..6 bracket the phases: pack | sort | bvh | cells | overflow | csr
@@ -117,6 +122,7 @@ static int check_config(const vd_config* c) {
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64) return VD_ERR_INVALID_ARG;
   if (c->counters < 0 || c->counters > 1 || c->timing < 0 || c->timing > 1) return VD_ERR_INVALID_ARG;
   if (c->warm_start < 0 || c->warm_start > 1) return VD_ERR_INVALID_ARG;
+  if (c->cell_mode < 0 || c->cell_mode > 1) return VD_ERR_INVALID_ARG;
   return VD_OK;
 }
 
@@ -353,6 +359,7 @@ int vd_default_config(vd_config* cfg) {
   cfg->counters = 0;
   cfg->timing = 0;
   cfg->warm_start = 0;
+  cfg->cell_mode = 0;
   return VD_OK;
 }
 
@@ -566,6 +573,162 @@ int vd_get_status(vd_ctx* ctx, vd_status* st) {
   st->refined_volumes = d.refined_volumes;
   for (int k = 0; k < 4; k++) st->overflow_reason[k] = d.ovf_reason[k];
   return VD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+//
+// Coordinate descent over the kernel form and its capacities: starting from
+// the context's configuration, each knob in turn (cell form, polytope
+// capacity, queue depth, leaf size, block size, warm start) takes each of
+// its other values; a trial is one warm-up build then the faster of two
+// timed builds (CUDA events on the caller's stream) of the caller's input,
+// and a value is kept if it is at least 2% faster. A configuration under
+// which a cell fails (error other than neighbour capacity) is skipped.
+static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::function<int(const vd_out*)>& build,
+                    int32_t max_trials, int32_t flags, vd_config* best, cudaStream_t s) {
+  const vd_config user = ctx->cfg;
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= n) lg++;
+  const auto key = std::make_tuple(lg, weighted, nsets > 1 ? 1 + (nsets > 64) : 0);
+  if (!(flags & VD_TUNE_FORCE)) {
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+      vd_config c = it->second;
+      c.counters = user.counters;
+      c.timing = user.timing;
+      c.cull_mode = user.cull_mode;
+      c.traversal = user.traversal;
+      ctx->cfg = c;
+      if (best) *best = c;
+      return VD_OK;
+    }
+  }
+  if (max_trials <= 0) max_trials = 16;
+  // scratch outputs of the trial builds
+  const int64_t cap = 24 * n + 4096;
+  vd_out o{};
+  char* mem = nullptr;
+  const size_t b_off = align_up(sizeof(int32_t) * (size_t)(n + 1)), b_nb = align_up(sizeof(int32_t) * (size_t)cap),
+               b_vol = align_up(sizeof(float) * (size_t)n), b_cen = align_up(sizeof(float) * 3 * (size_t)n);
+  if (cudaMalloc(&mem, b_off + b_nb + b_vol + b_cen + 512) != cudaSuccess) return VD_ERR_CUDA;
+  o.offsets = (int32_t*)mem;
+  o.neighbors = (int32_t*)(mem + b_off);
+  o.nnz_capacity = cap;
+  o.volume = (float*)(mem + b_off + b_nb);
+  o.centroid = (float*)(mem + b_off + b_nb + b_vol);
+  o.nnz_out = (int64_t*)(mem + b_off + b_nb + b_vol + b_cen);
+  o.status = (int32_t*)(mem + b_off + b_nb + b_vol + b_cen + 256);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int trials = 0;
+  auto trial = [&](vd_config c, float& ms) -> bool {
+    c.counters = 0;
+    c.timing = 0;
+    if (check_config(&c) != VD_OK) return false;
+    ctx->cfg = c;
+    trials++;
+    if (build(&o) != VD_OK) return false;
+    vd_status st;
+    if (vd_get_status(ctx, &st) != VD_OK) return false;
+    if (st.error != VD_OK && st.error != VD_ERR_CAPACITY) return false;
+    ms = INFINITY;
+    for (int r = 0; r < 2; r++) {
+      cudaEventRecord(e0, s);
+      if (build(&o) != VD_OK) return false;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = fminf(ms, t);
+    }
+    return true;
+  };
+  vd_config cur = user;
+  float cur_ms = INFINITY;
+  int rc = VD_OK;
+  if (!trial(cur, cur_ms)) {
+    // the starting point itself failed: fall back to the defaults
+    vd_default_config(&cur);
+    cur.cull_mode = user.cull_mode;
+    cur.traversal = user.traversal;
+    if (!trial(cur, cur_ms)) rc = VD_ERR_CELL_OVERFLOW;
+  }
+  if (rc == VD_OK) {
+    struct Knob {
+      int32_t vd_config::*field;
+      int values[3];
+      int count;
+      bool warp_only;
+    };
+    const Knob knobs[] = {
+        {&vd_config::cell_mode, {0, 1, 0}, 2, false},  {&vd_config::verts_per_lane, {2, 4, 0}, 2, true},
+        {&vd_config::queue_per_lane, {2, 4, 8}, 3, true}, {&vd_config::leaf_size, {8, 16, 32}, 3, false},
+        {&vd_config::warps_per_block, {2, 4, 8}, 3, true}, {&vd_config::warm_start, {0, 1, 0}, 2, true},
+    };
+    for (const Knob& k : knobs) {
+      if (k.warp_only && cur.cell_mode != 0) continue;
+      for (int v = 0; v < k.count && trials < max_trials; v++) {
+        if (cur.*(k.field) == k.values[v]) continue;
+        vd_config c = cur;
+        c.*(k.field) = k.values[v];
+        float ms = INFINITY;
+        if (trial(c, ms) && ms < 0.98f * cur_ms) {
+          cur = c;
+          cur_ms = ms;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(mem);
+  // the trial builds' outputs are gone: no forward state for vd_backward
+  ctx->have_forward = false;
+  cur.counters = user.counters;
+  cur.timing = user.timing;
+  if (rc != VD_OK) {
+    ctx->cfg = user;
+    return rc;
+  }
+  ctx->cfg = cur;
+  ctx->tuned[key] = cur;
+  if (best) *best = cur;
+  return VD_OK;
+}
+
+extern "C" {
+
+int vd_autotune(vd_ctx* ctx, const float* xyz, const float* weights, int64_t n, vd_box bbox, int32_t max_trials,
+                int32_t flags, vd_config* best, void* stream) {
+  if (!ctx || !xyz || n <= 0 || !box_ok(bbox)) return VD_ERR_INVALID_ARG;
+  if (n > kMaxSites) return VD_ERR_TOO_LARGE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  return autotune(
+      ctx, n, 1, weights ? 1 : 0, [&](const vd_out* o) { return vd_build(ctx, xyz, weights, n, bbox, o, stream); },
+      max_trials, flags, best, s);
+}
+
+int vd_autotune_batched(vd_ctx* ctx, const float* xyz, const float* weights, const int64_t* set_offsets,
+                        const vd_box* boxes, const uint8_t* weighted, int32_t nsets, int32_t max_trials, int32_t flags,
+                        vd_config* best, void* stream) {
+  if (!ctx || !xyz || !set_offsets || !boxes || nsets < 1 || nsets > kMaxSets) return VD_ERR_INVALID_ARG;
+  const int64_t n = set_offsets[nsets];
+  if (n <= 0) return VD_ERR_INVALID_ARG;
+  if (n > kMaxSites) return VD_ERR_TOO_LARGE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  int anyw = 0;
+  for (int k = 0; weights && weighted && k < nsets; k++) anyw |= weighted[k] ? 1 : 0;
+  return autotune(
+      ctx, n, nsets, anyw,
+      [&](const vd_out* o) {
+        return vd_build_batched(ctx, xyz, weights, set_offsets, boxes, weighted, nsets, o, stream);
+      },
+      max_trials, flags, best, (cudaStream_t)stream);
 }
 
 const char* vd_error_string(int code) {

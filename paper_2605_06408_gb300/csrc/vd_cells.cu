@@ -821,7 +821,9 @@ cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, cons
   cudaError_t err;
   const vd_config& g = c.cfg;
   const int q = g.queue_per_lane;
-  if (g.verts_per_lane >= 4) {
+  if (g.cell_mode == 1) {
+    err = launch_cells_thread(c, num_sms, s);
+  } else if (g.verts_per_lane >= 4) {
     err = q >= 8   ? launch_variant<4, 128, 8>(c, num_sms, s)
           : q >= 4 ? launch_variant<4, 128, 4>(c, num_sms, s)
           : q >= 2 ? launch_variant<4, 128, 2>(c, num_sms, s)

@@ -200,8 +200,10 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c, WarpSmem
 // dmin, dmax)) (tighter than the paper's dmin/2 for heavy sites). Culled
 // iff LB exceeds the cell radius over the octants the box occupies.
 // Returns keep; lb is a safe (padded) LB, key the best-first key LB - R.
-__device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* rtab, int cull_mode,
-                                          float& lb, int& occ, float& key) {
+// Radius lookup rad(occ) gives the cell radius over the occupied octants.
+template <typename RadiusOf>
+__device__ __forceinline__ bool node_test_r(float4 lo, float4 hi, float4 me, RadiusOf rad, int cull_mode, float& lb,
+                                            int& occ, float& key) {
   float rl[3] = {lo.x - me.x, lo.y - me.y, lo.z - me.z};
   float rh[3] = {hi.x - me.x, hi.y - me.y, hi.z - me.z};
   float d2 = 0.0f, f2 = 0.0f;
@@ -215,7 +217,7 @@ __device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const
     occ |= (rh[k] >= 0.0f ? 1 : 0) << (2 * k);
     occ |= (rl[k] <= 0.0f ? 1 : 0) << (2 * k + 1);
   }
-  float R = rtab[occ];
+  float R = rad(occ);
   float c = me.w - lo.w;
   float D = sqrtf(d2);
   if (c > 0.0f) D = fminf(fmaxf(sqrtf(c), D), sqrtf(f2) * (1.0f + kCullPad));
@@ -229,6 +231,11 @@ __device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const
   key = (D2 + c) / (2.0f * D) - R;
   if (cull_mode == 2) return true;
   return !(lb > R * (1.0f + kCullPad));
+}
+
+__device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* rtab, int cull_mode,
+                                          float& lb, int& occ, float& key) {
+  return node_test_r(lo, hi, me, [&](int o) { return rtab[o]; }, cull_mode, lb, occ, key);
 }
 
 template <int VPL, int PCAP, int QPL>

@@ -281,6 +281,7 @@ cudaError_t launch_gather_sites(const float* xyz, const float* w, const int* per
 cudaError_t launch_build_bvh(const uint64_t* keys, const float4* sites, int n, int leaf_size, BvhBuffers& b,
                              SetInfo* sets, int nsets, DevStatus* st, cudaStream_t s);
 cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, const std::function<void()>& between);
+cudaError_t launch_cells_thread(const CellBuffers& c, int num_sms, cudaStream_t s);
 cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbors, int64_t cap, int64_t* nnz_out,
                        long long* block_sums, int32_t* user_status, bool recount, cudaStream_t s);
 cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s);

@@ -27,8 +27,9 @@ VD_ERR_TOO_LARGE = -6
 ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
     "vd_build", "vd_copy_neighbors", "vd_build_batched", "vd_backward", "vd_get_timings", "vd_get_status",
-    "vd_error_string", "vd_cells_noalloc",
+    "vd_error_string", "vd_cells_noalloc", "vd_autotune", "vd_autotune_batched",
 )
+VD_TUNE_FORCE = 1
 
 
 class VdBox(ctypes.Structure):
@@ -59,6 +60,7 @@ class VdConfig(ctypes.Structure):
         ("counters", ctypes.c_int32),
         ("timing", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
+        ("cell_mode", ctypes.c_int32),
     ]
 
 
@@ -112,6 +114,9 @@ def load_library(build_if_missing: bool = True):
         lib.vd_get_status.argtypes = [P, ctypes.POINTER(VdStatus)]
         lib.vd_get_timings.argtypes = [P, ctypes.POINTER(VdTimings)]
         lib.vd_cells_noalloc.argtypes = [P, P, I64, VdBox, P, P, P, P, P, P]
+        lib.vd_autotune.argtypes = [P, P, P, I64, VdBox, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(VdConfig), P]
+        lib.vd_autotune_batched.argtypes = [P, P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(VdConfig), P]
         lib.vd_error_string.argtypes = [I]
         lib.vd_error_string.restype = ctypes.c_char_p
         for f in ABI_FUNCTIONS:
@@ -209,6 +214,44 @@ class Context:
         cs = _config_struct(merged)
         _check(self._lib.vd_set_config(self._h, ctypes.byref(cs)), "vd_set_config")
         self.config = merged
+
+    # ------------------------------------------------------------ autotuner
+    def autotune(self, sites: torch.Tensor, weights: Optional[torch.Tensor] = None, bbox=((0, 0, 0), (1, 1, 1)),
+                 max_trials: int = 0, force: bool = False) -> dict:
+        """Time candidate configurations of build() on this input (vd_autotune)
+        and keep the fastest; returns it. Synchronises; tune before capturing
+        a graph. A following backward() needs a new build()."""
+        sites = sites.contiguous()
+        weights = None if weights is None else weights.contiguous()
+        best = VdConfig()
+        rc = self._lib.vd_autotune(self._h, _ptr(sites), _ptr(weights), sites.shape[0], _box(bbox), int(max_trials),
+                                   VD_TUNE_FORCE if force else 0, ctypes.byref(best), _stream_ptr(self.device))
+        _check(rc, "vd_autotune")
+        self.config = {k: getattr(best, k) for k, _ in VdConfig._fields_}
+        return dict(self.config)
+
+    def autotune_batched(self, sites: torch.Tensor, weights: Optional[torch.Tensor], set_offsets: Sequence[int],
+                         boxes, weighted: Optional[Sequence[int]] = None, max_trials: int = 0,
+                         force: bool = False) -> dict:
+        """vd_autotune_batched: as autotune() for build_batched()."""
+        import numpy as np
+
+        sites = sites.contiguous()
+        offs = np.ascontiguousarray(np.asarray(set_offsets, dtype=np.int64))
+        nsets = offs.shape[0] - 1
+        bx = (VdBox * nsets)()
+        for k, b in enumerate(boxes):
+            bx[k] = _box(b)
+        wf = None if weighted is None else np.ascontiguousarray(np.asarray(weighted, dtype=np.uint8))
+        best = VdConfig()
+        rc = self._lib.vd_autotune_batched(self._h, _ptr(sites), _ptr(weights), offs.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.cast(bx, ctypes.c_void_p),
+                                           None if wf is None else wf.ctypes.data_as(ctypes.c_void_p), nsets,
+                                           int(max_trials), VD_TUNE_FORCE if force else 0, ctypes.byref(best),
+                                           _stream_ptr(self.device))
+        _check(rc, "vd_autotune_batched")
+        self.config = {k: getattr(best, k) for k, _ in VdConfig._fields_}
+        return dict(self.config)
 
     def reserve(self, n: int, weighted: bool = False):
         _check(self._lib.vd_reserve(self._h, int(n), int(weighted)), "vd_reserve")

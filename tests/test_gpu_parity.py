@@ -128,7 +128,9 @@ def test_configs_at_full_size_sampled(ctx):
 @pytest.mark.parametrize("cfg", [
     {"cull_mode": 2}, {"cull_mode": 1}, {"traversal": 1}, {"leaf_size": 1}, {"leaf_size": 32},
     {"verts_per_lane": 4, "queue_per_lane": 1}, {"verts_per_lane": 2, "queue_per_lane": 1},
-    {"warps_per_block": 8, "blocks_per_sm": 2},
+    {"warps_per_block": 8, "blocks_per_sm": 2}, {"warm_start": 1},
+    {"cell_mode": 1}, {"cell_mode": 1, "cull_mode": 1}, {"cell_mode": 1, "traversal": 1},
+    {"cell_mode": 1, "leaf_size": 8},
 ])
 def test_configuration_knobs_give_identical_cells(vdmod, cfg):
     x = W.mixture(6000, 21)

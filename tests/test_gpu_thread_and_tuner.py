@@ -1,0 +1,102 @@
+"""The thread-per-cell form (vd_config.cell_mode = 1, the paper's own
+mapping) against the FP64 oracle and the warp form, and the autotuner
+(vd_autotune / vd_autotune_batched) through the C ABI."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_06408_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vdmod():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_06408_gb300 import vd
+
+    vd.load_library()
+    return vd
+
+
+def dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def same_cells(a, b):
+    assert torch.equal(a.offsets, b.offsets)
+    assert torch.equal(a.neighbors, b.neighbors)
+    assert torch.allclose(a.volume, b.volume, rtol=1e-5, atol=0)
+    assert torch.allclose(a.centroid, b.centroid, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "power"])
+def test_thread_form_matches_oracle(vdmod, kind):
+    if kind == "uniform":
+        x, w, box = W.config("uniform10k")
+    else:
+        x = W.mixture(20000, 31)
+        w, box = W.power_weights(x, 32), W.UNIT_BOX
+    ctx = vdmod.Context(0, {"cell_mode": 1})
+    r = ctx.build(dev(x), dev(w), box)
+    st = ctx.status()
+    assert st["error"] == 0 and st["failed_cells"] == 0
+    ref = oracle.cells(x, w, box)
+    off = r.offsets.cpu().numpy().astype(np.int64)
+    nb = r.neighbors.cpu().numpy()
+    for i in range(len(x)):
+        assert np.array_equal(nb[off[i]:off[i + 1]], ref["nbrs"][i]), i
+    vol = r.volume.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(vol - ref["vol"]) <= 1e-5 * ref["vol"] + 1e-30)
+    cen = r.centroid.cpu().numpy().astype(np.float64)
+    assert np.all(np.linalg.norm(cen - ref["cen"], axis=1) <= 1e-5 * np.linalg.norm(ref["cen"], axis=1))
+
+
+def test_thread_form_batched_equals_warp_form(vdmod):
+    X, Wt, offs, flags = W.batched(3)
+    k = 24  # the first 24 sets (sizes 1e3..2e5, both kinds)
+    n = int(offs[k])
+    boxes = [W.UNIT_BOX] * k
+    a = vdmod.Context(0).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
+    b = vdmod.Context(0, {"cell_mode": 1}).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
+    same_cells(a, b)
+
+
+def test_autotune_single_set(vdmod):
+    x = W.mixture(200_000, 41)
+    w = W.power_weights(x, 42)
+    xs, ws = dev(x), dev(w)
+    ref = vdmod.Context(0).build(xs, ws, W.UNIT_BOX)
+    ctx = vdmod.Context(0)
+    cfg = ctx.autotune(xs, ws, W.UNIT_BOX, max_trials=10)
+    assert cfg["cell_mode"] in (0, 1) and cfg["verts_per_lane"] in (2, 4)
+    assert cfg["queue_per_lane"] in (1, 2, 4, 8) and 1 <= cfg["leaf_size"] <= 32
+    # no forward state after tuning
+    with pytest.raises(vdmod.VdError):
+        ctx.backward(torch.ones(len(x), device="cuda"), None)
+    same_cells(ctx.build(xs, ws, W.UNIT_BOX), ref)
+    # cached: the same key returns at once with the same configuration
+    t0 = time.perf_counter()
+    again = ctx.autotune(xs, ws, W.UNIT_BOX)
+    assert time.perf_counter() - t0 < 0.05
+    assert again == cfg
+    # forced: re-tuned, still valid
+    forced = ctx.autotune(xs, ws, W.UNIT_BOX, max_trials=3, force=True)
+    assert forced["verts_per_lane"] in (2, 4)
+
+
+def test_autotune_batched(vdmod):
+    X, Wt, offs, flags = W.batched(3)
+    k = 16
+    n = int(offs[k])
+    boxes = [W.UNIT_BOX] * k
+    ref = vdmod.Context(0).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
+    ctx = vdmod.Context(0)
+    cfg = ctx.autotune_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k], max_trials=6)
+    assert cfg["cell_mode"] in (0, 1)
+    same_cells(ctx.build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k]), ref)
