@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=300_000, help="cells in the oracle's timed sample")
     p.add_argument("--config", default="", help="JSON dict of libvd config overrides")
+    p.add_argument("--no-autotune", action="store_true", help="skip vd_autotune before the timed steps")
+    p.add_argument("--no-forms", action="store_true", help="skip the plain-FP32 and per-set comparisons")
+    p.add_argument("--accuracy-sample", type=int, default=20_000, help="cells checked against the oracle")
     return p.parse_args()
 
 
@@ -231,6 +234,28 @@ def kernel_source_hash() -> str:
     return hsh.hexdigest()[:16]
 
 
+def accuracy(res, x, w, box, sample: int, base: int = 0, seed: int = 11):
+    """Neighbour lists, volumes and centroids of `sample` seeded cells of
+    the set x (rows base + i of res) against the FP64 oracle."""
+    import oracle
+    from paper_2605_06408_gb300 import workloads as W
+
+    m = min(sample, len(x))
+    cells = np.sort(W.rng_for(seed).choice(len(x), m, replace=False))
+    ref = oracle.cells(x, w, box, cells=cells)
+    off = res.offsets.cpu().numpy().astype(np.int64)
+    nb = res.neighbors.cpu().numpy()
+    vol = res.volume.cpu().numpy().astype(np.float64)[base + cells]
+    cen = res.centroid.cpu().numpy().astype(np.float64)[base + cells]
+    bad = sum(not np.array_equal(nb[off[base + i]:off[base + i + 1]], ref["nbrs"][q]) for q, i in enumerate(cells))
+    rv = ref["vol"]
+    nz = rv > 0
+    ve = float(np.max(np.abs(vol[nz] - rv[nz]) / rv[nz])) if nz.any() else 0.0
+    ce = float(np.max(np.linalg.norm(cen - ref["cen"], axis=1) / np.linalg.norm(ref["cen"], axis=1)))
+    return {"cells": int(m), "neighbour_lists_differing": int(bad), "max_volume_rel_err": ve,
+            "max_centroid_rel_err": ce}
+
+
 def run_ours(args):
     import torch
 
@@ -262,6 +287,17 @@ def run_ours(args):
             return c.build(xs, wts, box, nnz_capacity=cap, sync=sync)
         return c.build_batched(xs, wts, batch[0], batch[1], batch[2], nnz_capacity=cap, sync=sync)
 
+    # autotune (outside the timed region): the configuration the steps use
+    tune_s = None
+    if not args.no_autotune:
+        t0 = time.time()
+        if batch is None:
+            ctx.autotune(sites, weights, box)
+        else:
+            ctx.autotune_batched(sites, weights, batch[0], batch[1], batch[2])
+        tune_s = time.time() - t0
+    cfg = dict(ctx.config)
+
     # warm-up (also sizes the workspace and the neighbour buffer)
     res = None
     for _ in range(max(args.warmup, 1)):
@@ -292,7 +328,7 @@ def run_ours(args):
     if batch is not None:
         # batched steps replay one captured launch sequence (vd_build_batched
         # enqueues kernels, async copies and memsets only)
-        gctx = vd.Context(local, dict(cfg, timing=0))
+        gctx = vd.Context(local, dict(cfg, timing=0))  # the tuned configuration
         gctx.reserve(n, weights is not None)
         side = torch.cuda.Stream(dev)
         side.wait_stream(stream)
@@ -334,6 +370,61 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     ms = statistics.mean(step_ms)
+    ms_min = min(step_ms)
+
+    # ---- the same build in plain FP32, and (batched) as one build per set
+    forms = None
+    if not args.no_forms and rank == 0:
+        def timed(fn, reps=3):
+            fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.mean(ts)
+
+        f32 = vd.Context(local, dict(cfg, timing=0, precision=1))
+        f32_ms = timed(lambda: build(f32, sites, weights, cap, sync=False))
+        r32 = build(f32, sites, weights, cap)
+        if batch is None:
+            ax, aw, abase = x, w, 0
+        else:  # the largest set
+            offs = batch[0]
+            s_big = int(np.argmax(np.diff(offs)))
+            abase = int(offs[s_big])
+            ax = x[offs[s_big]:offs[s_big + 1]]
+            aw = w[offs[s_big]:offs[s_big + 1]] if batch[2][s_big] else None
+        forms = {
+            "mixed_fp32_fp64": {"mcells_s": n / (ms * 1e-3) / 1e6,
+                                "accuracy": accuracy(res, ax, aw, box, args.accuracy_sample, abase)},
+            "plain_fp32": {"mcells_s": n / (f32_ms * 1e-3) / 1e6, "ms_per_step": f32_ms,
+                           "accuracy": accuracy(r32, ax, aw, box, args.accuracy_sample, abase)},
+        }
+        del f32, r32
+        if batch is not None:
+            offs = batch[0]
+            per = vd.Context(local, dict(cfg, timing=0))
+            views = []
+            for s in range(len(offs) - 1):
+                a, b = int(offs[s]), int(offs[s + 1])
+                views.append((sites[a:b], None if (weights is None or not batch[2][s]) else weights[a:b],
+                              batch[1][s]))
+
+            def per_set():
+                for xs, wt, bx in views:
+                    per.build(xs, wt, bx, sync=False)
+
+            per_ms = timed(per_set, reps=2)
+            forms["per_set_builds"] = {"mcells_s": n / (per_ms * 1e-3) / 1e6, "ms_per_step": per_ms,
+                                       "builds": len(views), "note": "one vd_build per set, same stream"}
+            del per
 
     # ---- forward + backward
     fb_ms = None
@@ -440,6 +531,7 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": ms,
+        "ms_per_step_min": ms_min,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -448,7 +540,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": n,
                    "weighted": w is not None, "l2": "flushed between timed steps (256 MiB write)",
                    "timed_step": "CUDA graph replay" if graph is not None else "eager vd_build",
-                   "libvd": {k: v for k, v in ctx.config.items()}},
+                   "libvd": {k: v for k, v in ctx.config.items()},
+                   "autotuned": not args.no_autotune, "autotune_s": tune_s},
         "fwd_bwd_mcells_s": None if fb_ms is None else total_cells / (fb_ms * 1e-3) / 1e6,
         "fwd_bwd_ms_per_step": fb_ms,
         "e2e": {"value": total_cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
@@ -466,6 +559,7 @@ def run_ours(args):
         "status": {k: st[k] for k in ("empty_cells", "overflow_cells", "failed_cells", "fp64_fallbacks",
                                       "fp64_ambiguous")},
         "cpu_baseline": cpu,
+        "forms": forms,
     }
     print(json.dumps(out))
     if dist is not None:

@@ -98,6 +98,13 @@ typedef struct {
                            /*    (the paper's mapping, App. A.3: 64 vertices, 48    */
                            /*    planes, 48 queue entries per cell); cells beyond   */
                            /*    either capacity go to the large-cell pass          */
+  int32_t precision;       /* 0: mixed (default): FP32 predicates, those within     */
+                           /*    their error bound of zero re-evaluated in FP64,    */
+                           /*    ill-conditioned vertices re-solved and suspect     */
+                           /*    volumes re-integrated in FP64;                     */
+                           /* 1: plain FP32 (no FP64 step; for comparison only:     */
+                           /*    neighbour lists may then differ from the exact     */
+                           /*    diagram on near-degenerate inputs)                 */
 } vd_config;
 
 /* Device-side results of the last call, read back by vd_get_status. */
@@ -234,8 +241,8 @@ const char* vd_error_string(int code);
  * verts_per_lane (polytope capacity), queue_per_lane (queue depth),
  * leaf_size, warps_per_block and warm_start; each trial is one warm-up and
  * two timed builds (CUDA events), a change is kept if >= 2% faster, at most
- * max_trials trials (<= 0: 16). cull_mode, traversal, counters and timing
- * stay the caller's. The result is cached in ctx per (floor(log2 n), any
+ * max_trials trials (<= 0: 16). cull_mode, traversal, precision, counters
+ * and timing stay the caller's. The result is cached in ctx per (floor(log2 n), any
  * set weighted, set-count class); a later call with the same key returns
  * the cached configuration without trials unless flags has VD_TUNE_FORCE.
  *

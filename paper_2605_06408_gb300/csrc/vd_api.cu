@@ -123,6 +123,7 @@ static int check_config(const vd_config* c) {
   if (c->counters < 0 || c->counters > 1 || c->timing < 0 || c->timing > 1) return VD_ERR_INVALID_ARG;
   if (c->warm_start < 0 || c->warm_start > 1) return VD_ERR_INVALID_ARG;
   if (c->cell_mode < 0 || c->cell_mode > 1) return VD_ERR_INVALID_ARG;
+  if (c->precision < 0 || c->precision > 1) return VD_ERR_INVALID_ARG;
   return VD_OK;
 }
 
@@ -360,6 +361,7 @@ int vd_default_config(vd_config* cfg) {
   cfg->timing = 0;
   cfg->warm_start = 0;
   cfg->cell_mode = 0;
+  cfg->precision = 0;
   return VD_OK;
 }
 
@@ -600,6 +602,7 @@ static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::
       c.timing = user.timing;
       c.cull_mode = user.cull_mode;
       c.traversal = user.traversal;
+      c.precision = user.precision;
       ctx->cfg = c;
       if (best) *best = c;
       return VD_OK;
@@ -654,6 +657,7 @@ static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::
     vd_default_config(&cur);
     cur.cull_mode = user.cull_mode;
     cur.traversal = user.traversal;
+    cur.precision = user.precision;
     if (!trial(cur, cur_ms)) rc = VD_ERR_CELL_OVERFLOW;
   }
   if (rc == VD_OK) {

@@ -91,6 +91,7 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
   const unsigned lane = lane_id();
   C c;
   c.me = P.sites[si];
+  c.fp64 = P.cfg.precision == 0;
   const int orig_i = P.perm[si];
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
@@ -255,6 +256,7 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
   const unsigned lane = lane_id();
   BigCell c;
   c.me = P.sites[si];
+  c.fp64 = P.cfg.precision == 0;
   const int orig_i = P.perm[si];
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];

@@ -150,6 +150,7 @@ struct BigCell {
   int npl, qn, seq;
   int nst;  // candidate planes staged in A.hs for the next filter
   bool dirty;
+  bool fp64;  // FP64 re-evaluation of ambiguous predicates, vertices and volumes
 };
 
 __device__ __forceinline__ bool bdead(uint64_t T) { return (T & kTriMask) == kTriMask; }
@@ -680,7 +681,7 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
           if (!bdead(T[u])) {
             float s = side<float>(H, v[u].x, v[u].y, v[u].z);
             out = s > 0.0f;
-            if (ambiguous<float>(s, v[u].w, H.e)) {
+            if (c.fp64 && ambiguous<float>(s, v[u].w, H.e)) {
               ct.fp64++;
               out = big_resolve64(A, T[u], hpid, c.me, c.lo, c.hi, sites, ct.fp64amb);
             }
@@ -741,7 +742,7 @@ static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float
       if (slot < kBigV) {
         float x, y, z, ev;
         vertex3<float>(big_plane(A, (int)a), big_plane(A, (int)b), H, x, y, z, ev);
-        if (!(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
+        if (c.fp64 && !(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
           refine_vertex(A.pid[a], A.pid[b], hpid, c.me, c.lo, c.hi, sites, x, y, z, ev);
           ct.refv++;
         }

@@ -95,6 +95,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   const bool counters = P.cfg.counters != 0;
   C c;
   c.me = P.sites[si];
+  c.fp64 = P.cfg.precision == 0;
   const int orig_i = P.perm[si];
   if (P.loser[si]) {  // an exact duplicate site owns this position
     if (lane == 0) {
@@ -281,7 +282,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   L = sqrtf(L);
   double ox = cx, oy = cy, oz = cz;
   double Vd = V;
-  if (volume_needs_fp64(V, L, Sabs, emax)) {
+  if (c.fp64 && volume_needs_fp64(V, L, Sabs, emax)) {
     double Mxd, Myd, Mzd;
     volume_fp64(S, nv, c.me, c.box, c.box + 3, P.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
     if (Vd > 0.0) {
@@ -547,7 +548,7 @@ __device__ inline void big_volume(const BigCell& c, const BigArena& A, const flo
   oy = cy;
   oz = cz;
   V = Vf;
-  if (!volume_needs_fp64(Vf, L, Sabs, emax)) {
+  if (!c.fp64 || !volume_needs_fp64(Vf, L, Sabs, emax)) {
     if (Vf > 0.f) {
       ox += Mx / Vf;
       oy += My / Vf;
@@ -609,6 +610,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
   const bool counters = P.cfg.counters != 0;
   BigCell c;
   c.me = P.sites[si];
+  c.fp64 = P.cfg.precision == 0;
   const int orig_i = P.perm[si];
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];

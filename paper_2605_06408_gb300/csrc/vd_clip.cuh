@@ -70,6 +70,7 @@ struct Cell {
   uint32_t freem[NPW];
   int qn, seq;
   bool dirty;
+  bool fp64;  // FP64 re-evaluation of ambiguous predicates, vertices and volumes
 };
 
 template <int VPL, int PCAP, int QPL>
@@ -329,7 +330,7 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, c
     if (c.vt[r] != kEmptyTri) {
       float s = side<float>(H, c.vx[r], c.vy[r], c.vz[r]);
       out[r] = s > 0.0f;
-      if (ambiguous<float>(s, c.ve[r], H.e)) {
+      if (c.fp64 && ambiguous<float>(s, c.ve[r], H.e)) {
         atomicAdd(&S.ct.fp64, 1u);
         out[r] = resolve64(S, c.vt[r], hpid, c.me, c.box, c.box + 3, sites);
       }
@@ -421,7 +422,7 @@ __device__ int clip_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, c
         PlaneT<float> A = load_plane(S, (int)a), B = load_plane(S, (int)b);
         float x, y, z, ev;
         vertex3<float>(A, B, H, x, y, z, ev);
-        if (!(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
+        if (c.fp64 && !(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
           refine_vertex(S.pid[a], S.pid[b], hpid, c.me, c.box, c.box + 3, sites, x, y, z, ev);
           atomicAdd(&S.ct.refv, 1u);
         }

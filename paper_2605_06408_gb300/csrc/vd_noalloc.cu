@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t*
     CellT c;
     c.me = sites[i];
     c.box = SC->box;
+    c.fp64 = true;
     bool empty = SC->loser[i] != 0, overflow = false;
     if (!empty) init_cell(c, S, 0);
     for (int base = 0; base < n && !empty && !overflow; base += 32) {
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t*
     for (int k = 0; k < 3; k++) L += fmaxf(c.alo[k] * c.alo[k], c.ahi[k] * c.ahi[k]);
     L = sqrtf(L);
     double ox = cx, oy = cy, oz = cz, Vd = V;
-    if (volume_needs_fp64(V, L, Sabs, emax)) {
+    if (c.fp64 && volume_needs_fp64(V, L, Sabs, emax)) {
       double Mxd, Myd, Mzd;
       volume_fp64(S, nv, c.me, c.box, c.box + 3, sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
       if (Vd > 0.0) {

@@ -33,6 +33,7 @@ struct TCell {
   const float* hi;
   float alo[3], ahi[3], sc[3], srad;
   int nv, npl, qn, seq;
+  bool fp64;  // FP64 re-evaluation of ambiguous predicates, vertices and volumes
 };
 
 __device__ __forceinline__ PlaneT<float> t_plane(const TCell& C, int k) {
@@ -156,7 +157,7 @@ __device__ int t_clip(TCell& C, const PlaneT<float>& H, int hpid, const float4* 
     const float4 p = C.vp[v];
     const float s = side<float>(H, p.x, p.y, p.z);
     bool o = s > 0.0f;
-    if (ambiguous<float>(s, p.w, H.e)) {
+    if (C.fp64 && ambiguous<float>(s, p.w, H.e)) {
       ct.fp64++;
       o = t_resolve64(C, C.vt[v], hpid, sites, ct.fp64amb);
     }
@@ -203,7 +204,7 @@ __device__ int t_clip(TCell& C, const PlaneT<float>& H, int hpid, const float4* 
       if (C.nv >= kTV) return CLIP_OVERFLOW;
       float x, y, z, ev;
       vertex3<float>(t_plane(C, (int)a), t_plane(C, (int)b), H, x, y, z, ev);
-      if (!(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
+      if (C.fp64 && !(ev <= kRefineRel * (fabsf(x) + fabsf(y) + fabsf(z)))) {
         refine_vertex(C.pid[a], C.pid[b], hpid, C.me, C.lo, C.hi, sites, x, y, z, ev);
         ct.refv++;
       }
@@ -317,7 +318,7 @@ __device__ bool t_outputs(TCell& C, const CellBuffers& P, int orig_i, int setfir
   for (int k = 0; k < 3; k++) L += fmaxf(C.alo[k] * C.alo[k], C.ahi[k] * C.ahi[k]);
   L = sqrtf(L);
   double ox = cx, oy = cy, oz = cz, Vd = V;
-  if (volume_needs_fp64(V, L, Sabs, emax)) {
+  if (C.fp64 && volume_needs_fp64(V, L, Sabs, emax)) {
     // FP64: vertices re-solved from the inputs; each face's fan anchored at
     // its lowest-index vertex
     ct.refvol++;
@@ -435,6 +436,7 @@ __device__ bool t_build_cell(const CellBuffers& P, int si, Counters& ct, long lo
   const SetInfo& SI = P.sets[set];
   TCell C;
   C.me = me;
+  C.fp64 = P.cfg.precision == 0;
   C.lo = SI.lo;
   C.hi = SI.hi;
   t_init(C);

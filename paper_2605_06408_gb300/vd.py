@@ -61,6 +61,7 @@ class VdConfig(ctypes.Structure):
         ("timing", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
         ("cell_mode", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
     ]
 
 
