@@ -43,6 +43,14 @@ WORKLOADS = {
                    "full ncu captures",
     "surfaces20M": "Voronoi of 20,000,000 sites in nested Gaussian shells (sigma 1e-2..1e-5) around 32 "
                    "random surfaces + 1% background, seed 4",
+    "power200k": "power diagram of 200,000 mixture sites (seed 1) with the power1M weight law (seed 2); the "
+                 "small case used for ncu captures of the large-cell kernel",
+    "uniform1M": "Voronoi of 1,000,000 uniform sites (the paper's white-noise case, Sec. 5.1), seed 5",
+    "gradient1M": "Voronoi of 1,000,000 sites with density linear in x (the paper's gradient case), seed 5",
+    "clustered1M_K10": "Voronoi of 1,000,000 sites in 10 isotropic Gaussian clusters, sigma = 0.005 of the box "
+                       "(the paper's K=10, sigma=0.1 in [-10,10]^3), clamped to the box, seed 6",
+    "clustered1M_K5": "as clustered1M_K10 with 5 clusters",
+    "gaussw_uniform1M": "power diagram of uniform1M with the paper's weights w ~ N(0, (d_nn^2/3)^2), seed 7",
     "batched256": "256 independent sets, sizes log-uniform in [1e3, 2e5] (~9M sites), odd sets power "
                   "(w = r^2, r = 0.2 nn exp(N(0,1))), uniform or mixture per set, seed 3; one build_batched "
                   "per step, replayed from a CUDA graph",
@@ -107,6 +115,18 @@ def _single_workload(name: str, seed_shift: int):
         return W.mixture(200_000, 1 + seed_shift), None, W.UNIT_BOX
     if name == "surfaces20M":
         return W.surfaces(20_000_000, 4 + seed_shift), None, W.UNIT_BOX
+    if name == "power200k":
+        x = W.mixture(200_000, 1 + seed_shift)
+        return x, W.power_weights(x, 2 + seed_shift), W.UNIT_BOX
+    if name == "uniform1M":
+        return W.uniform(1_000_000, 5 + seed_shift), None, W.UNIT_BOX
+    if name == "gradient1M":
+        return W.gradient(1_000_000, 5 + seed_shift), None, W.UNIT_BOX
+    if name in ("clustered1M_K10", "clustered1M_K5"):
+        return W.clustered(1_000_000, 10 if name.endswith("K10") else 5, 6 + seed_shift), None, W.UNIT_BOX
+    if name == "gaussw_uniform1M":
+        x = W.uniform(1_000_000, 5 + seed_shift)
+        return x, W.gaussian_weights(x, 7 + seed_shift), W.UNIT_BOX
     raise KeyError(name)
 
 

@@ -105,6 +105,28 @@ def mixture(n: int, seed: int = 1, clusters: int = 64, background: float = 0.10)
     return np.ascontiguousarray(out[rng.permutation(n)])
 
 
+def clustered(n: int, clusters: int, seed: int = 6, sigma: float = 0.005) -> np.ndarray:
+    """The paper's clustered test case (Sec. 5.1) scaled to the unit box:
+    `clusters` centres uniform in the box, sites split evenly among them,
+    isotropic Gaussian with sigma = 0.1 / 20 (0.1 in the paper's [-10, 10]^3),
+    clamped to the box; float32, deduped."""
+    rng = rng_for(seed)
+    centres = rng.random((clusters, 3))
+
+    def draw(m):
+        per = np.full(clusters, m // clusters)
+        per[: m - per.sum()] += 1
+        lab = np.repeat(np.arange(clusters), per)
+        p = centres[lab] + sigma * rng.standard_normal((m, 3))
+        return np.clip(p, 0.0, 1.0).astype(np.float32)
+
+    out = dedupe(draw(n))
+    while out.shape[0] < n:
+        out = dedupe(np.concatenate([out, draw(n - out.shape[0] + 16)]))
+    out = out[:n]
+    return np.ascontiguousarray(out[rng.permutation(n)])
+
+
 def nearest_neighbour_distance(x: np.ndarray) -> np.ndarray:
     """Each site's distance to its nearest other site (float64)."""
     from scipy.spatial import cKDTree

@@ -80,7 +80,7 @@ def test_uniform_10k_full(ctx):
     assert st["error"] == 0 and st["failed_cells"] == 0 and st["fp64_ambiguous"] == 0
 
 
-@pytest.mark.parametrize("kind", ["mixture", "power", "surfaces", "gradient", "gaussian_w"])
+@pytest.mark.parametrize("kind", ["mixture", "power", "surfaces", "gradient", "gaussian_w", "clustered"])
 def test_workloads_100k_full(ctx, kind):
     n = 100_000
     w = None
@@ -92,6 +92,8 @@ def test_workloads_100k_full(ctx, kind):
         x = W.surfaces(n, 13)
     elif kind == "gradient":
         x = W.gradient(n, 14)
+    elif kind == "clustered":  # the paper's K=10 case: many sites clamped onto the box faces
+        x = W.clustered(n, 10, 17)
     else:
         x = W.uniform(n, 15)
         w = W.gaussian_weights(x, 16)
