@@ -143,6 +143,7 @@ struct BigCell {
   float lo[3], hi[3];
   float alo[3], ahi[3];
   float sc[3], srad;
+  float em;      // largest vertex error bound
   int nv;        // vertex slots in use (live and dead)
   int nlive;     // live vertices
   int nfree;     // dead slots on the free-slot stack
@@ -502,6 +503,7 @@ __device__ inline void big_aabb(BigCell& c, const BigArena& A, int cull_mode) {
     r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
   }
   c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
+  c.em = em;
   fill_rtab(A.rtab, c.alo, c.ahi, c.sc, c.srad, cull_mode);
 }
 

@@ -406,6 +406,10 @@ __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
 
 // ---------------------------------------------------------------- large cells
 
+// Polytopes of at most this many vertex slots take the cone bound of a BVH
+// child from their vertices (exact support); larger ones from the chunk boxes.
+constexpr int kConeExactMax = 512;
+
 // Filter the staged candidate planes against the polytope; clip by those
 // that may cut, nearest plane first. Returns CLIP_EMPTY / CLIP_OVERFLOW, or
 // CLIP_NONE (c.dirty set if the polytope changed).
@@ -673,6 +677,52 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
         float key0 = __shfl_sync(FULL, key, 0), key1 = __shfl_sync(FULL, key, 2);
         int r0 = __shfl_sync(FULL, myref, 0), r1 = __shfl_sync(FULL, myref, 2);
         if (counters) ct.nodes += 2;
+        if ((k0 || k1) && cull == 0) {
+          // cone bound of each surviving child, the cell's support in the
+          // cone axis taken over the vertices (small polytopes) or the chunk
+          // boxes
+          const float rmax = sqrtf(c.sc[0] * c.sc[0] + c.sc[1] * c.sc[1] + c.sc[2] * c.sc[2]) + c.srad;
+          const int nch = (c.nv + 31) >> 5;
+#pragma unroll
+          for (int ch = 0; ch < 2; ch++) {
+            const bool kc = ch == 0 ? k0 : k1;
+            if (!kc) continue;
+            const int src = 2 * ch;
+            float4 blo, bhi;
+            blo.x = __shfl_sync(FULL, rec.x, src);
+            blo.y = __shfl_sync(FULL, rec.y, src);
+            blo.z = __shfl_sync(FULL, rec.z, src);
+            bhi.x = __shfl_sync(FULL, hi.x, src);
+            bhi.y = __shfl_sync(FULL, hi.y, src);
+            bhi.z = __shfl_sync(FULL, hi.z, src);
+            const float lbc = __shfl_sync(FULL, lb, src);
+            Cone k;
+            if (!node_cone(blo, bhi, c.me, k)) continue;
+            float h = -INFINITY;
+            if (c.nv <= kConeExactMax) {
+              // exact support over the vertices (dead slots are NaN: ignored)
+              for (int i = (int)lane; i < c.nv; i += 32) {
+                const float4 v = A.vp[i];
+                h = fmaxf(h, fmaf(k.ux, v.x, fmaf(k.uy, v.y, k.uz * v.z)));
+              }
+            } else {
+              for (int q = (int)lane; q < nch; q += 32) {
+                const float4 qlo = A.cb[2 * q], qhi = A.cb[2 * q + 1];
+                if (!(qlo.x <= qhi.x)) continue;  // every slot of the chunk dead
+                const float sx = k.ux >= 0.0f ? qhi.x : qlo.x, sy = k.uy >= 0.0f ? qhi.y : qlo.y,
+                            sz = k.uz >= 0.0f ? qhi.z : qlo.z;
+                h = fmaxf(h, fmaf(k.ux, sx, fmaf(k.uy, sy, k.uz * sz)));
+              }
+            }
+            h = warp_maxf(h);
+            if (cone_culls(lbc, h, c.em, rmax, k)) {
+              if (ch == 0)
+                k0 = false;
+              else
+                k1 = false;
+            }
+          }
+        }
         if (k0 && k1) {
           bool near0 = trav == 1 ? true : key0 <= key1;
           int fsrc = near0 ? 2 : 0;

@@ -66,6 +66,7 @@ struct Cell {
   const float* box;  // the set's box: lo[3] then hi[3] (global memory)
   float alo[3], ahi[3];
   float sc[3], srad;  // bounding sphere of the cell (local frame)
+  float em;           // largest vertex error bound
   int nv;
   uint32_t freem[NPW];
   int qn, seq;
@@ -190,6 +191,7 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c, WarpSmem
       r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
   c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
+  c.em = em;
   fill_rtab(S.rtab, c.alo, c.ahi, c.sc, c.srad, cull_mode);
 }
 
@@ -237,6 +239,38 @@ __device__ __forceinline__ bool node_test_r(float4 lo, float4 hi, float4 me, Rad
 __device__ __forceinline__ bool node_test(float4 lo, float4 hi, float4 me, const float* rtab, int cull_mode,
                                           float& lb, int& occ, float& key) {
   return node_test_r(lo, hi, me, [&](int o) { return rtab[o]; }, cull_mode, lb, occ, key);
+}
+
+// Cone bound of a child box [lo, hi] (local frame after subtracting the
+// site): every site j in the box has its plane normal n_j within the cone of
+// axis u (toward the box centre) and half-angle theta (the cone tangent to
+// the box's circumscribed ball), and its plane can cut the cell only if
+// d_ij < h(n_j), the cell's support in direction n_j. The support function
+// is Lipschitz with constant max|v|, so h(n_j) <= h(u) + 2 sin(theta/2) max|v|.
+// Returns false when the cone is every direction (the site inside the ball).
+struct Cone {
+  float ux, uy, uz, slack_per_r;  // axis, 2 sin(theta/2)
+};
+__device__ __forceinline__ bool node_cone(float4 lo, float4 hi, float4 me, Cone& k) {
+  const float cx = 0.5f * (lo.x + hi.x) - me.x, cy = 0.5f * (lo.y + hi.y) - me.y, cz = 0.5f * (lo.z + hi.z) - me.z;
+  const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+  const float d2 = cx * cx + cy * cy + cz * cz;
+  const float r2 = (hx * hx + hy * hy + hz * hz) * (1.0f + 1e-4f);
+  if (!(d2 > 1.0001f * r2) || !(d2 > 0.0f)) return false;
+  const float id = rsqrtf(d2);
+  k.ux = cx * id;
+  k.uy = cy * id;
+  k.uz = cz * id;
+  // cos(theta) = sqrt(1 - r^2/d^2); 2 sin(theta/2) = sqrt(2 - 2 cos(theta))
+  const float ct = sqrtf(fmaxf(0.0f, 1.0f - r2 / d2));
+  k.slack_per_r = sqrtf(fmaxf(0.0f, 2.0f - 2.0f * ct)) * (1.0f + 1e-4f) + 1e-6f;
+  return true;
+}
+// Culled iff the padded LB exceeds the cone bound (support h in direction
+// u, plus the vertex error bound and the Lipschitz slack).
+__device__ __forceinline__ bool cone_culls(float lb, float h, float em, float rmax, const Cone& k) {
+  const float R = h + em + k.slack_per_r * rmax;
+  return lb > R * (1.0f + kCullPad) + kCullPad * rmax;
 }
 
 template <int VPL, int PCAP, int QPL>
