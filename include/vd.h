@@ -53,6 +53,8 @@ extern "C" {
 #define VD_ERR_CELL_OVERFLOW (-4) /* a cell exceeded the largest polytope capacity    */
 #define VD_ERR_NO_FORWARD (-5)    /* vd_backward without a matching forward build     */
 #define VD_ERR_TOO_LARGE (-6)     /* more sites than the index encoding supports      */
+#define VD_ERR_TIMEOUT (-7)       /* a bounded wait between warps of a block ran out   */
+                                  /*   (device side; outputs of that build not valid)  */
 
 /* ------------------------------------------------------------------ types */
 typedef struct vd_ctx vd_ctx;

@@ -751,6 +751,8 @@ const char* vd_error_string(int code) {
       return "no forward build in this context";
     case VD_ERR_TOO_LARGE:
       return "too many sites or neighbours for the index encoding";
+    case VD_ERR_TIMEOUT:
+      return "a bounded wait between warps of a block ran out (build not valid)";
     default:
       return "unknown error";
   }

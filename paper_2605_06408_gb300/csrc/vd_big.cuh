@@ -70,6 +70,8 @@ struct BigArena {
   float* hord;     // [32] their clip order key (plane offset)
   uint32_t* hist;  // [kDirBins] direction-bin counts / cursors
   uint32_t* cdirty;  // [kBigC / 32] chunks whose box is stale
+  struct HelpBoard* hb;  // the block's helping board (forward large-cell kernel only)
+  int* err;              // device error word
 };
 
 constexpr int kDirBins = 6 * 64;
@@ -135,6 +137,8 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   A.hord = (float*)(w + 32 * 16 + 2 * 32 * 4);
   A.hist = (uint32_t*)(w + 32 * 16 + 3 * 32 * 4);
   A.cdirty = (uint32_t*)(w + 32 * 16 + 3 * 32 * 4 + kDirBins * 4);
+  A.hb = nullptr;
+  A.err = nullptr;
   return A;
 }
 
@@ -392,10 +396,10 @@ constexpr int kBoxStage = 2;
 // test reaches its box. A plane that leaves every vertex certainly inside
 // also leaves every later (clipped, smaller) polytope of the cell inside, so
 // the caller drops it for good.
-// The staged planes of mask m, four per step so that their shared-memory
-// loads and tests overlap; f(t, H) is called for each.
+// The staged planes (hs, hse) of mask m, four per step so that their
+// shared-memory loads and tests overlap; f(t, H) is called for each.
 template <typename F>
-__device__ __forceinline__ void for_staged_planes(const BigArena& A, uint32_t m, F f) {
+__device__ __forceinline__ void for_staged_planes(const float4* hs, const float* hse, uint32_t m, F f) {
   while (m) {
     int t[4];
 #pragma unroll
@@ -407,12 +411,12 @@ __device__ __forceinline__ void for_staged_planes(const BigArena& A, uint32_t m,
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       const int tt = t[u] < 0 ? t[0] : t[u];
-      const float4 h = A.hs[tt];
+      const float4 h = hs[tt];
       H[u].nx = h.x;
       H[u].ny = h.y;
       H[u].nz = h.z;
       H[u].b = h.w;
-      H[u].e = A.hse[tt];
+      H[u].e = hse[tt];
     }
 #pragma unroll
     for (int u = 0; u < 4; u++)
@@ -420,21 +424,24 @@ __device__ __forceinline__ void for_staged_planes(const BigArena& A, uint32_t m,
   }
 }
 
-__device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k, Counters& ct, bool counters) {
+// Which of the planes in `open` (staged at hs / hse) leave a vertex of the
+// chunks [q0, q1) outside or ambiguous? Chunk boxes are tested first when
+// `boxes`; each flagged chunk's vertices are loaded once for all the planes
+// whose test reaches its box.
+__device__ inline uint32_t filter_chunks(const float4* vp, const float4* cb, int nv, int q0, int q1,
+                                         const float4* hs, const float* hse, uint32_t open, bool boxes,
+                                         long long& tested) {
   const unsigned lane = lane_id();
-  uint32_t open = k >= 32 ? FULL : ((1u << k) - 1u);
   uint32_t cuts = 0;
-  long long tested = 0;
-  const int nch = (c.nv + 31) >> 5;
-  for (int cbase = 0; cbase < nch && open; cbase += 32) {
+  for (int cbase = q0; cbase < q1 && open; cbase += 32) {
     const int q = cbase + (int)lane;
     uint32_t fl = 0;
-    if (q < nch) {
-      if (nch <= kBoxStage) {
+    if (q < q1) {
+      if (!boxes) {
         fl = open;
       } else {
-        const float4 lo = A.cb[2 * q], hi = A.cb[2 * q + 1];
-        for_staged_planes(A, open, [&](int t, const PlaneT<float>& H) {
+        const float4 lo = cb[2 * q], hi = cb[2 * q + 1];
+        for_staged_planes(hs, hse, open, [&](int t, const PlaneT<float>& H) {
           if (chunk_may_cut(H, lo, hi)) fl |= 1u << t;
         });
       }
@@ -453,15 +460,15 @@ __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k
         if (qs[u] < 0) pms[u] = 0;
         const int i = 32 * (cbase + (qs[u] < 0 ? 0 : qs[u])) + (int)lane;
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pms[u] && i < c.nv) v[u] = A.vp[i];
+        if (pms[u] && i < nv) v[u] = vp[i];
       }
       uint32_t outm = 0;
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int i = 32 * (cbase + (qs[u] < 0 ? 0 : qs[u])) + (int)lane;
-        if (i < c.nv) {
+        if (i < nv) {
           const float4 w = v[u];
-          for_staged_planes(A, pms[u], [&](int t, const PlaneT<float>& H) {
+          for_staged_planes(hs, hse, pms[u], [&](int t, const PlaneT<float>& H) {
             const float s = side<float>(H, w.x, w.y, w.z);
             if (s > 0.0f || ambiguous<float>(s, w.w, H.e)) outm |= 1u << t;
           });
@@ -473,8 +480,171 @@ __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k
       open &= ~outm;
     }
   }
+  return cuts;
+}
+
+// ---------------------------------------------------------------- helping
+//
+// Warps of a large-cell block that have run out of cells help the others'
+// batch filters (the dominant step of cells with thousands of vertices).
+// The owner posts a request (its planes stay in its shared memory, its
+// vertex and chunk arrays in its arena); every warp of the block, the owner
+// included, claims groups of kHelpGroup chunks by compare-and-swap on a
+// counter tagged with the request's generation, ORs the planes it finds
+// cutting into the request and then counts the chunks done; the owner
+// closes the request once every chunk is done. A claim succeeds only while
+// its generation is open and chunks remain, and the owner cannot close
+// before every claimed group is counted, so a helper never works on a
+// request that was closed or re-opened under it. Waits are bounded: a wait
+// that runs out sets VD_ERR_TIMEOUT and returns.
+struct HelpReq {
+  int seq;        // odd while open
+  int next;       // generation << 20 | next unclaimed chunk
+  int done;       // chunks finished
+  unsigned cuts;  // planes found cutting
+  int nch, k, nv, pad;
+  const float4* vp;
+  const float4* cb;
+  const float4* hs;
+  const float* hse;
+};
+struct HelpBoard {
+  HelpReq req[kBigWarpsPerBlock];
+  int live;  // warps of the block still building their own cells
+};
+constexpr int kHelpMinChunks = 64;  // filters over fewer chunks run alone
+constexpr int kHelpGroup = 16;      // chunks per claim
+constexpr long long kWaitLimit = 1ll << 24;
+
+__device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
+
+__device__ inline void set_error_timeout(const BigArena& A) {
+  if (A.err) atomicCAS(A.err, 0, VD_ERR_TIMEOUT);
+}
+
+// Lane 0: claim the next group of request r (generation gen); -1 if none.
+__device__ inline int help_claim(HelpReq& r, int gen, int nch) {
+  int old = vload(&r.next);
+  while (true) {
+    if ((old >> 20) != gen) return -1;
+    const int idx = old & 0xfffff;
+    if (idx >= nch) return -1;
+    const int prev = atomicCAS(&r.next, old, old + kHelpGroup);
+    if (prev == old) return idx;
+    old = prev;
+  }
+}
+
+// Work on request r through its groups; returns the number of groups done
+// once none is left to claim.
+__device__ inline int help_drain(HelpReq& r, int gen, long long& tested) {
+  const unsigned lane = lane_id();
+  int groups = 0;
+  while (true) {
+    int q0 = -1;
+    if (lane == 0) q0 = help_claim(r, gen, vload(&r.nch));
+    q0 = __shfl_sync(FULL, q0, 0);
+    if (q0 < 0) return groups;
+    groups++;
+    // the request is open and unchanged while a claimed group is uncounted
+    const int nch = vload(&r.nch), k = vload(&r.k), nv = vload(&r.nv);
+    const float4* vp = r.vp;
+    const float4* cb = r.cb;
+    const float4* hs = r.hs;
+    const float* hse = r.hse;
+    const uint32_t open = (k >= 32 ? FULL : ((1u << k) - 1u)) & ~(uint32_t)vload((const int*)&r.cuts);
+    const int q1 = min(nch, q0 + kHelpGroup);
+    const uint32_t cm = filter_chunks(vp, cb, nv, q0, q1, hs, hse, open, true, tested);
+    if (lane == 0) {
+      if (cm) atomicOr(&r.cuts, cm);
+      __threadfence_block();
+      atomicAdd(&r.done, q1 - q0);
+    }
+    __syncwarp();
+  }
+}
+
+// Batch filter: which of the k <= 32 planes staged in A.hs / A.hse may
+// cut the polytope (some vertex outside or ambiguous)? Bit t of the result
+// stands for plane t. A plane that leaves every vertex certainly inside
+// also leaves every later (clipped, smaller) polytope of the cell inside, so
+// the caller drops it for good.
+__device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k, Counters& ct, bool counters) {
+  const unsigned lane = lane_id();
+  const uint32_t open = k >= 32 ? FULL : ((1u << k) - 1u);
+  long long tested = 0;
+  const int nch = (c.nv + 31) >> 5;
+  uint32_t cuts;
+  // post a request only when some warp of the block has no cell of its own
+  bool share = A.hb != nullptr && nch >= kHelpMinChunks;
+  if (share) share = __shfl_sync(FULL, vload(&A.hb->live), 0) < (int)(blockDim.x >> 5);
+  if (!share) {
+    cuts = filter_chunks(A.vp, A.cb, c.nv, 0, nch, A.hs, A.hse, open, nch > kBoxStage, tested);
+  } else {
+    HelpReq& r = A.hb->req[threadIdx.x >> 5];
+    int gen = 0;
+    if (lane == 0) {
+      gen = ((vload(&r.seq) >> 1) + 1) & 0x7ff;
+      r.nch = nch;
+      r.k = k;
+      r.nv = c.nv;
+      r.vp = A.vp;
+      r.cb = A.cb;
+      r.hs = A.hs;
+      r.hse = A.hse;
+      r.done = 0;
+      r.cuts = 0;
+      r.next = gen << 20;
+      __threadfence_block();  // the arena's vertices and boxes and the request fields before the opening
+      atomicAdd(&r.seq, 1);
+    }
+    gen = __shfl_sync(FULL, gen, 0);
+    help_drain(r, gen, tested);
+    if (lane == 0) {
+      long long it = 0;
+      while (vload(&r.done) < nch) {
+        __nanosleep(32);
+        if (++it > kWaitLimit) {
+          set_error_timeout(A);
+          break;
+        }
+      }
+      __threadfence_block();
+    }
+    __syncwarp();
+    cuts = (uint32_t)vload((const int*)&r.cuts);
+    cuts = __shfl_sync(FULL, cuts, 0);
+    if (lane == 0) atomicAdd(&r.seq, 1);
+    __syncwarp();
+  }
   if (counters) ct.vtests += tested;
   return cuts;
+}
+
+// A warp that has no cell left helps the block's open requests until every
+// warp of the block has finished its own cells (bounded wait).
+__device__ inline void big_help(const BigArena& A, long long& tested) {
+  const unsigned lane = lane_id();
+  const int me = (int)(threadIdx.x >> 5);
+  if (lane == 0) atomicSub(&A.hb->live, 1);
+  long long it = 0;
+  while (true) {
+    bool worked = false;
+    for (int w = 0; w < kBigWarpsPerBlock; w++) {
+      if (w == me) continue;
+      HelpReq& r = A.hb->req[w];
+      int s = vload(&r.seq);
+      s = __shfl_sync(FULL, s, 0);
+      if (!(s & 1)) continue;
+      if (help_drain(r, ((s >> 1) + 1) & 0x7ff, tested) > 0) worked = true;
+    }
+    if (worked) continue;
+    int live = vload(&A.hb->live);
+    live = __shfl_sync(FULL, live, 0);
+    if (live <= 0) break;
+    __nanosleep(256);
+    if (++it > kWaitLimit) break;
+  }
 }
 
 __device__ inline void big_aabb(BigCell& c, const BigArena& A, int cull_mode) {

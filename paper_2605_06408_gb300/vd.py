@@ -23,6 +23,7 @@ VD_ERR_CAPACITY = -3
 VD_ERR_CELL_OVERFLOW = -4
 VD_ERR_NO_FORWARD = -5
 VD_ERR_TOO_LARGE = -6
+VD_ERR_TIMEOUT = -7
 
 ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
