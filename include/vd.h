@@ -100,6 +100,16 @@ typedef struct {
                            /*    (the paper's mapping, App. A.3: 64 vertices, 48    */
                            /*    planes, 48 queue entries per cell); cells beyond   */
                            /*    either capacity go to the large-cell pass          */
+  int32_t tape;            /* 1: a warp-per-cell forward also keeps each cell it     */
+                           /*    builds in registers (up to 48 vertices and 32      */
+                           /*    faces) on a tape of 1 KB per site for              */
+                           /*    vd_backward(recompute = 0), if the tape fits in    */
+                           /*    half of the free device memory when the workspace  */
+                           /*    is sized; otherwise, and with 0 (default: no       */
+                           /*    backward planned), the adjoint re-clips every cell */
+                           /*    (memory asks for recomputing). Set it when a       */
+                           /*    backward follows: the tape costs ~3% of a forward  */
+                           /*    and saves ~half of the adjoint                     */
   int32_t precision;       /* 0: mixed (default): FP32 predicates, those within     */
                            /*    their error bound of zero re-evaluated in FP64,    */
                            /*    ill-conditioned vertices re-solved and suspect     */
@@ -217,9 +227,13 @@ int vd_build_batched(vd_ctx* ctx, const float* sites_xyz, const float* weights, 
  *   grad_centroid : DEVICE float32 [3n] or NULL.
  *   grad_sites    : DEVICE float32 [3n], overwritten.
  *   grad_weights  : DEVICE float32 [n] or NULL, overwritten.
- *   recompute     : must be 1: each cell is re-clipped from its stored
- *                   neighbour list (no traversal).
- * Errors: VD_ERR_NO_FORWARD if the context holds no forward build. */
+ *   recompute     : 1: every cell is re-clipped from its stored neighbour
+ *                   list (no traversal); 0: cells the forward kept on the
+ *                   tape (vd_config.tape) are read from it, the others are
+ *                   re-clipped (with no tape this equals 1). Both give the
+ *                   same gradients up to FP32 rounding of the vertices.
+ * Errors: VD_ERR_NO_FORWARD if the context holds no forward build;
+ * VD_ERR_INVALID_ARG if recompute is not 0 or 1. */
 int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
                 float* grad_weights, int recompute, void* stream);
 

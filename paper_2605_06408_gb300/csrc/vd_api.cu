@@ -92,6 +92,10 @@ struct vd_ctx {
   bool ev_valid = false;
   bool ev_backward = false;
   int launches = 0;
+  // tape of the forward's cells for the adjoint (separate allocation)
+  char* tape = nullptr;
+  int64_t tape_cap = 0;
+  bool tape_valid = false;
   // autotuner: best configuration per (log2 n, weighted, set count)
   std::map<std::tuple<int, int, int>, vd_config> tuned;
 };
@@ -124,12 +128,17 @@ static int check_config(const vd_config* c) {
   if (c->warm_start < 0 || c->warm_start > 1) return VD_ERR_INVALID_ARG;
   if (c->cell_mode < 0 || c->cell_mode > 1) return VD_ERR_INVALID_ARG;
   if (c->precision < 0 || c->precision > 1) return VD_ERR_INVALID_ARG;
+  if (c->tape < 0 || c->tape > 1) return VD_ERR_INVALID_ARG;
   return VD_OK;
 }
 
 static int release(vd_ctx* ctx) {
   if (ctx->base) cudaFree(ctx->base);
   ctx->base = nullptr;
+  if (ctx->tape) cudaFree(ctx->tape);
+  ctx->tape = nullptr;
+  ctx->tape_cap = 0;
+  ctx->tape_valid = false;
   ctx->bytes = 0;
   ctx->cap_n = 0;
   ctx->have_forward = false;
@@ -170,8 +179,31 @@ static Layout make_layout(int64_t n, int num_sms) {
   return L;
 }
 
+// The tape (1 KB per site) when the configuration asks for it and it fits in
+// half of the free device memory; otherwise none (the adjoint re-clips).
+static void reserve_tape(vd_ctx* ctx) {
+  const bool want = ctx->cfg.tape != 0 && ctx->cfg.cell_mode == 0;
+  if (!want || ctx->tape_cap >= ctx->cap_n) return;
+  if (ctx->tape) cudaFree(ctx->tape);
+  ctx->tape = nullptr;
+  ctx->tape_cap = 0;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return;
+  const size_t bytes = (size_t)kTapeStride * (size_t)ctx->cap_n;
+  if (bytes > free_b / 2) return;
+  if (cudaMalloc(&ctx->tape, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->tape = nullptr;
+    return;
+  }
+  ctx->tape_cap = ctx->cap_n;
+}
+
 static int reserve(vd_ctx* ctx, int64_t n) {
-  if (n <= ctx->cap_n && ctx->base) return VD_OK;
+  if (n <= ctx->cap_n && ctx->base) {
+    reserve_tape(ctx);
+    return VD_OK;
+  }
   int64_t want = n;
   if (ctx->cap_n > 0 && want < ctx->cap_n + ctx->cap_n / 4) want = ctx->cap_n + ctx->cap_n / 4;
   if (want > kMaxSites) want = kMaxSites;
@@ -216,6 +248,7 @@ static int reserve(vd_ctx* ctx, int64_t n) {
   ctx->wrange = (unsigned*)(ctx->work + 8);
   ctx->st = (DevStatus*)(b + L.off[23]);
   ctx->sets_dev = (SetInfo*)(b + L.off[24]);
+  reserve_tape(ctx);
   return VD_OK;
 }
 
@@ -243,6 +276,7 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   c.work = ctx->work;
   c.st = ctx->st;
   c.cfg = ctx->cfg;
+  c.tape = (ctx->cfg.tape && ctx->cfg.cell_mode == 0 && ctx->tape_cap >= ctx->last_n) ? ctx->tape : nullptr;
   return c;
 }
 
@@ -337,6 +371,7 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   if (e != cudaSuccess) return VD_ERR_CUDA;
   mark(ctx, 6, s);
   ctx->have_forward = true;
+  ctx->tape_valid = c.tape != nullptr;
   ctx->last_stream = s;
   ctx->ev_valid = ctx->cfg.timing != 0;
   ctx->ev_backward = false;
@@ -361,6 +396,7 @@ int vd_default_config(vd_config* cfg) {
   cfg->timing = 0;
   cfg->warm_start = 0;
   cfg->cell_mode = 0;
+  cfg->tape = 0;
   cfg->precision = 0;
   return VD_OK;
 }
@@ -493,7 +529,7 @@ int vd_build_batched(vd_ctx* ctx, const float* xyz, const float* weights, const 
 
 int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
                 float* grad_weights, int recompute, void* stream) {
-  if (!ctx || !grad_sites || recompute != 1) return VD_ERR_INVALID_ARG;
+  if (!ctx || !grad_sites || (recompute != 0 && recompute != 1)) return VD_ERR_INVALID_ARG;
   if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -513,6 +549,7 @@ int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroi
   b.list_count = ctx->work + 4;
   b.list_cap = ctx->ovf_cap;
   b.work = ctx->work + 2;
+  b.tape = (recompute == 0 && ctx->tape_valid) ? ctx->tape : nullptr;
   ctx->ev_valid = false;
   mark(ctx, 0, s);
   cudaError_t e = launch_backward(b, ctx->num_sms, s);
@@ -603,6 +640,7 @@ static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::
       c.cull_mode = user.cull_mode;
       c.traversal = user.traversal;
       c.precision = user.precision;
+      c.tape = user.tape;
       ctx->cfg = c;
       if (best) *best = c;
       return VD_OK;

@@ -98,6 +98,49 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
   c.box = SI.lo;
   const int cnt = P.counts[orig_i];
   if (cnt <= 0) return true;  // empty cell (or no site faces): no moving face
+  float sx, sy, sz;
+  uint32_t alive[NPW];
+  int nv = -1;
+  if (B.tape) {
+    // the forward's cell from the tape: vertices and face planes (the planes
+    // recomputed from their ids exactly as the forward computed them)
+    const char* rec = B.tape + (size_t)si * kTapeStride;
+    const int4 h = *reinterpret_cast<const int4*>(rec);
+    if (h.x > 0) {
+      nv = h.x;
+      const int nf = h.y;
+      const float4* tv = reinterpret_cast<const float4*>(rec + kTapeVOff);
+      const int* tf = reinterpret_cast<const int*>(rec + kTapeFOff);
+      sx = sy = sz = 0.f;
+      for (int t = (int)lane; t < nv; t += 32) {
+        const float4 r = tv[t];
+        S.nvp[t] = make_float4(r.x, r.y, r.z, 0.f);
+        S.nvt[t] = __float_as_uint(r.w);
+        sx += r.x;
+        sy += r.y;
+        sz += r.z;
+      }
+      for (int k = (int)lane; k < nf; k += 32) {
+        const int id = tf[k];
+        PlaneT<float> H;
+        if (id >= 0) {
+          const float4 q = P.sites[id];
+          H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+        } else {
+          H = box_plane<float>(-1 - id, c.me.x, c.me.y, c.me.z, c.box, c.box + 3);
+        }
+        S.pl[k] = make_float4(H.nx, H.ny, H.nz, H.b);
+        S.pid[k] = id;
+      }
+#pragma unroll
+      for (int w = 0; w < NPW; w++) alive[w] = nf >= 32 * (w + 1) ? FULL : (nf > 32 * w ? ((1u << (nf - 32 * w)) - 1u) : 0u);
+      sx = warp_sumf(sx);
+      sy = warp_sumf(sy);
+      sz = warp_sumf(sz);
+      __syncwarp();
+    }
+  }
+  if (nv < 0) {
   init_cell(c, S, 0);
   const int slot = P.ovf_slot[orig_i];
   if (slot >= 0) return false;  // a long neighbour list: the large-cell adjoint
@@ -134,9 +177,8 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
       if (rc == CLIP_EMPTY) return true;
     }
   }
-  float sx, sy, sz;
-  uint32_t alive[NPW];
-  const int nv = gather_vertices(c, S, sx, sy, sz, alive);
+  nv = gather_vertices(c, S, sx, sy, sz, alive);
+  }
   const float cx = sx / nv, cy = sy / nv, cz = sz / nv;
   for (int f = (int)lane; f < PCAP; f += 32)
 #pragma unroll

@@ -239,6 +239,41 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
     for (int u = 0; u < nvals; u++) rank += (int)S.otri[u] < v;
     row[rank] = v;
   }
+  if (P.tape) {
+    // the cell for the adjoint: vertices with plane indices renumbered to
+    // the alive planes' order, and those planes' ids
+    char* rec = P.tape + (size_t)si * kTapeStride;
+    int pre[NPW], nf = 0;
+#pragma unroll
+    for (int w = 0; w < NPW; w++) {
+      pre[w] = nf;
+      nf += __popc(alive[w]);
+    }
+    const bool fits = nv <= kTapeV && nf <= kTapeF;
+    if (fits) {
+      auto rank = [&](uint32_t f) -> uint32_t {
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < NPW; w++)
+          if ((f >> 5) == (uint32_t)w) r = (uint32_t)pre[w] + __popc(alive[w] & ((1u << (f & 31u)) - 1u));
+        return r;
+      };
+      float4* tv = reinterpret_cast<float4*>(rec + kTapeVOff);
+      for (int t = (int)lane; t < nv; t += 32) {
+        const uint32_t T = S.nvt[t];
+        const uint32_t R = rank(T & 255u) | (rank((T >> 8) & 255u) << 8) | (rank((T >> 16) & 255u) << 16);
+        const float4 p = S.nvp[t];
+        tv[t] = make_float4(p.x, p.y, p.z, __uint_as_float(R));
+      }
+      int* tf = reinterpret_cast<int*>(rec + kTapeFOff);
+#pragma unroll
+      for (int w = 0; w < NPW; w++) {
+        const int f = 32 * w + (int)lane;
+        if ((alive[w] >> lane) & 1u) tf[rank((uint32_t)f)] = S.pid[f];
+      }
+    }
+    if (lane == 0) *reinterpret_cast<int4*>(rec) = make_int4(fits ? nv : -1, nf, 0, 0);
+  }
   // volume and first moment: tetrahedra (c, g_f, v, w) for every directed
   // edge v -> w of face f (w = the other end of the edge), g_f = the foot of
   // c on plane f; c = vertex mean
@@ -387,6 +422,7 @@ __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
     int reason = 0;
     if (!build_cell<VPL, PCAP, QPL>(P, S, si, row, empties, reason)) {
       overflows++;
+      if (P.tape && lane == 0) *reinterpret_cast<int4*>(P.tape + (size_t)si * kTapeStride) = make_int4(-1, 0, 0, 0);
       if (lane == 0) atomicAdd((unsigned long long*)&P.st->ovf_reason[reason], 1ull);
       if (lane == 0) {
         int slot = atomicAdd(&P.st->ovf_count, 1);

@@ -227,6 +227,17 @@ struct BvhBuffers {
   float4* nodes;       // [n-1][4] traversal records
 };
 
+// Tape of the forward's cells for the adjoint: one record of kTapeStride
+// bytes per sorted site: int4 header (vertex count, face count; vertex count
+// -1 = no record, the adjoint re-clips), kTapeV float4 vertices (local
+// position, plane triplet bits in w, indices into the record's faces), kTapeF
+// face ids (sorted site index, or -1-f for box face f).
+constexpr int kTapeV = 48;
+constexpr int kTapeF = 32;
+constexpr int kTapeStride = 1024;
+constexpr int kTapeVOff = 16;
+constexpr int kTapeFOff = kTapeVOff + 16 * kTapeV;
+
 struct CellBuffers {
   const float4* sites;   // sorted packed sites
   const unsigned char* loser;  // sorted index: an exact duplicate site beats it
@@ -250,6 +261,7 @@ struct CellBuffers {
   float* cen;
   int* work;             // [2] work counters (main pass, overflow pass)
   DevStatus* st;
+  char* tape;            // [n * kTapeStride] or nullptr (no tape this build)
   vd_config cfg;
 };
 
@@ -267,6 +279,7 @@ struct BackBuffers {
   int* list_count;
   int list_cap;
   int* work;            // [2]
+  const char* tape;     // the forward's tape, or nullptr (re-clip every cell)
 };
 
 cudaError_t launch_weight_range(const float* w, int n, const SetInfo* sets, int nsets, unsigned* wr,

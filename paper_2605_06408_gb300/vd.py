@@ -62,6 +62,7 @@ class VdConfig(ctypes.Structure):
         ("timing", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
         ("cell_mode", ctypes.c_int32),
+        ("tape", ctypes.c_int32),
         ("precision", ctypes.c_int32),
     ]
 
@@ -348,7 +349,7 @@ class Context:
 
     # ------------------------------------------------------------ backward
     def backward(self, grad_volume: Optional[torch.Tensor], grad_centroid: Optional[torch.Tensor],
-                 want_weights: bool = True):
+                 want_weights: bool = True, recompute: bool = False):
         """Gradients (float32 [n,3], float32 [n] or None) of
         sum gv_i V_i + gc_i . g_i for the last build of this context."""
         n = self._last_n
@@ -356,7 +357,8 @@ class Context:
         gw = torch.empty(n, dtype=torch.float32, device=self.device) if want_weights else None
         gv = None if grad_volume is None else grad_volume.contiguous().float()
         gc = None if grad_centroid is None else grad_centroid.contiguous().float()
-        rc = self._lib.vd_backward(self._h, _ptr(gv), _ptr(gc), _ptr(gp), _ptr(gw), 1, _stream_ptr(self.device))
+        rc = self._lib.vd_backward(self._h, _ptr(gv), _ptr(gc), _ptr(gp), _ptr(gw), 1 if recompute else 0,
+                                   _stream_ptr(self.device))
         _check(rc, "vd_backward")
         return gp, gw
 
@@ -396,5 +398,8 @@ def cells(sites: torch.Tensor, weights: Optional[torch.Tensor] = None, bbox=((0,
     """Differentiable build: returns (volume, centroid, offsets, neighbors).
     Gradients flow from volume and centroid to sites and weights with the
     cell combinatorics held fixed."""
-    ctx = context or Context(sites.device.index or 0)
-    return _CellsFn.apply(sites, weights, ctx, bbox)
+    if context is None:
+        # a backward is planned when any input needs a gradient: keep the tape
+        grad = sites.requires_grad or (weights is not None and weights.requires_grad)
+        context = Context(sites.device.index or 0, {"tape": 1} if grad else None)
+    return _CellsFn.apply(sites, weights, context, bbox)

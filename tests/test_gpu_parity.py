@@ -270,3 +270,41 @@ def test_autograd_function(vdmod):
     d = 2 * cen.detach().cpu().numpy().astype(np.float64)
     ogp, _, _ = oracle.grad(x, None, W.UNIT_BOX, c, d)
     np.testing.assert_allclose(sites.grad.cpu().numpy(), ogp, rtol=1e-3, atol=1e-3 * np.abs(ogp).max())
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_backward_tape_equals_recompute(vdmod, weighted):
+    """The adjoint from the forward's tape and from re-clipped cells: both
+    match the oracle's analytic gradient on a subset, and each other up to
+    FP32 rounding of the vertices (ill-conditioned power cells amplify it)."""
+    x = W.mixture(50_000, 61)
+    w = W.power_weights(x, 62) if weighted else None
+    c, d = W.loss_coefficients(len(x), 63)
+    gv, gc = dev(c.astype(np.float32)), dev(d.astype(np.float32))
+    ctx = vdmod.Context(0, {"tape": 1})
+    res = build(ctx, x, w)
+    gp_t, gw_t = ctx.backward(gv, gc, want_weights=weighted)
+    gp_r, gw_r = ctx.backward(gv, gc, want_weights=weighted, recompute=True)
+    # both against the oracle on 150 cells and their neighbours
+    off = res.offsets.cpu().numpy().astype(np.int64)
+    nb = res.neighbors.cpu().numpy()
+    K = np.sort(W.rng_for(64).choice(len(x), 150, replace=False))
+    K = K[np.diff(off)[K] > 0]
+    cells = np.unique(np.concatenate([K] + [nb[off[q]:off[q + 1]] for q in K]))
+    ogp, _, _ = oracle.grad(x, w, W.UNIT_BOX, c, d, cells=cells)
+    for g in (gp_t, gp_r):
+        gg = g.cpu().numpy()[K].astype(np.float64)
+        err = np.abs(gg - ogp[K]).max(1) / np.maximum(np.abs(ogp[K]).max(1), 1e-30)
+        assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
+    # tape vs recompute on every site
+    scale = gp_r.abs().max(dim=1).values.clamp_min(1e-30)
+    rel = (gp_t - gp_r).abs().max(dim=1).values / scale
+    assert rel.quantile(0.999).item() < 1e-3 and rel.max().item() < 0.05
+    if weighted:
+        sw = gw_r.abs().clamp_min(1e-3 * gw_r.abs().max().item())
+        assert ((gw_t - gw_r).abs() / sw).quantile(0.99).item() < 1e-3
+    # a context without a tape re-clips: the same as recompute
+    nt = vdmod.Context(0, {"tape": 0})
+    build(nt, x, w)
+    gp_n, _ = nt.backward(gv, gc, want_weights=weighted)
+    assert torch.allclose(gp_n, gp_r, rtol=1e-5, atol=1e-6 * gp_r.abs().max().item())

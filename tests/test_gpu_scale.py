@@ -97,7 +97,7 @@ def test_backward_at_1M(vdmod, weighted):
     x = W.mixture(1_000_000, 1)
     w = W.power_weights(x, 2) if weighted else None
     c, d = W.loss_coefficients(len(x), 4)
-    ctx = vdmod.Context(0)
+    ctx = vdmod.Context(0, {"tape": 1})  # the adjoint reads the forward's cells
     res = ctx.build(dev(x), dev(w), W.UNIT_BOX)
     gp, gw = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=weighted)
     assert ctx.status()["error"] == 0
@@ -106,7 +106,7 @@ def test_backward_at_1M(vdmod, weighted):
 
 def test_surfaces_20M_forward_and_backward(vdmod):
     x = W.surfaces(20_000_000, 4)
-    ctx = vdmod.Context(0)
+    ctx = vdmod.Context(0, {"tape": 1})
     res = ctx.build(dev(x), None, W.UNIT_BOX)
     st = ctx.status()
     assert st["error"] == 0 and st["failed_cells"] == 0
