@@ -51,6 +51,8 @@ WORKLOADS = {
                        "(the paper's K=10, sigma=0.1 in [-10,10]^3), clamped to the box, seed 6",
     "clustered1M_K5": "as clustered1M_K10 with 5 clusters",
     "gaussw_uniform1M": "power diagram of uniform1M with the paper's weights w ~ N(0, (d_nn^2/3)^2), seed 7",
+    "uniform1M_wratio": "power diagram of uniform1M with w ~ N(0, (r d_nn^2)^2), r = --weight-ratio (the paper's "
+                        "weight-ratio sweep, on uniform sites), seed 7",
     "batched256": "256 independent sets, sizes log-uniform in [1e3, 2e5] (~9M sites), odd sets power "
                   "(w = r^2, r = 0.2 nn exp(N(0,1))), uniform or mixture per set, seed 3; one build_batched "
                   "per step, replayed from a CUDA graph",
@@ -78,6 +80,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true", help="skip vd_autotune before the timed steps")
     p.add_argument("--no-forms", action="store_true", help="skip the plain-FP32 and per-set comparisons")
     p.add_argument("--accuracy-sample", type=int, default=20_000, help="cells checked against the oracle")
+    p.add_argument("--weight-ratio", type=float, default=1.0 / 3.0, help="r of the uniform1M_wratio workload")
     return p.parse_args()
 
 
@@ -99,6 +102,9 @@ def make_workload(name: str, rank: int):
         return X, Wt, W.UNIT_BOX, (offs, [W.UNIT_BOX] * (len(offs) - 1), flags)
     x, w, box = _single_workload(name, seed_shift)
     return x, w, box, None
+
+
+WEIGHT_RATIO = 1.0 / 3.0
 
 
 def _single_workload(name: str, seed_shift: int):
@@ -127,6 +133,9 @@ def _single_workload(name: str, seed_shift: int):
     if name == "gaussw_uniform1M":
         x = W.uniform(1_000_000, 5 + seed_shift)
         return x, W.gaussian_weights(x, 7 + seed_shift), W.UNIT_BOX
+    if name == "uniform1M_wratio":
+        x = W.uniform(1_000_000, 5 + seed_shift)
+        return x, W.gaussian_weights(x, 7 + seed_shift, ratio=WEIGHT_RATIO), W.UNIT_BOX
     raise KeyError(name)
 
 
@@ -564,7 +573,8 @@ def run_ours(args):
                    "weighted": w is not None, "l2": "flushed between timed steps (256 MiB write)",
                    "timed_step": "CUDA graph replay" if graph is not None else "eager vd_build",
                    "libvd": {k: v for k, v in ctx.config.items()},
-                   "autotuned": not args.no_autotune, "autotune_s": tune_s},
+                   "autotuned": not args.no_autotune, "autotune_s": tune_s,
+                   "weight_ratio": args.weight_ratio if args.workload == "uniform1M_wratio" else None},
         "fwd_bwd_mcells_s": None if fb_ms is None else total_cells / (fb_ms * 1e-3) / 1e6,
         "fwd_bwd_config": "the timed configuration with tape = 1 (the forward keeps its cells for the adjoint)",
         "fwd_bwd_ms_per_step": fb_ms,
@@ -591,7 +601,9 @@ def run_ours(args):
 
 
 def main():
+    global WEIGHT_RATIO
     args = parse()
+    WEIGHT_RATIO = args.weight_ratio
     if args.impl == "reference":
         run_reference(args)
     else:

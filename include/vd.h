@@ -86,7 +86,8 @@ typedef struct {
   int32_t queue_per_lane;  /* best-first queue capacity per cell = 32 * this (1,2,4,8)*/
   int32_t cull_mode;       /* 0 directional (Sec. 4.2.1), 1 isotropic (single       */
                            /*   radius, ablation), 2 none (every site is clipped)   */
-  int32_t traversal;       /* 0 best-first (Alg. 1), 1 depth-first (ablation)        */
+  int32_t traversal;       /* 0 best-first (Alg. 1), 1 depth-first (ablation: the    */
+                           /*    nearer child first, backtracking last-in first-out)*/
   int32_t warps_per_block; /* persistent kernel block size in warps (1..8)           */
   int32_t blocks_per_sm;   /* persistent kernel grid = SMs * this (0 = occupancy)    */
   int32_t counters;        /* 1: count tests, clips and nodes (small overhead)       */

@@ -174,7 +174,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
         int r0 = __shfl_sync(FULL, myref, 0), r1 = __shfl_sync(FULL, myref, 2);
         if (counters && lane == 0) S.ct.nodes += 2;
         if (k0 && k1) {
-          bool near0 = trav == 1 ? true : key0 <= key1;
+          bool near0 = key0 <= key1;  // nearer child first (both traversals)
           int fsrc = near0 ? 2 : 0;
           float flb = __shfl_sync(FULL, lb, fsrc);
           int focc = __shfl_sync(FULL, occ, fsrc);
@@ -765,7 +765,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
           }
         }
         if (k0 && k1) {
-          bool near0 = trav == 1 ? true : key0 <= key1;
+          bool near0 = key0 <= key1;  // nearer child first (both traversals)
           int fsrc = near0 ? 2 : 0;
           float flb = __shfl_sync(FULL, lb, fsrc);
           int focc = __shfl_sync(FULL, occ, fsrc);

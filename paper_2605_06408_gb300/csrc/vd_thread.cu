@@ -470,7 +470,7 @@ __device__ bool t_build_cell(const CellBuffers& P, int si, Counters& ct, long lo
         const int r0 = __float_as_int(hi0.w), r1 = __float_as_int(hi1.w);
         ct.nodes += 2;
         if (k0 && k1) {
-          const bool near0 = trav == 1 ? true : key0 <= key1;
+          const bool near0 = key0 <= key1;  // nearer child first (both traversals)
           cur = near0 ? r0 : r1;
           if (!t_push(C, near0 ? lb1 : lb0, near0 ? r1 : r0, near0 ? occ1 : occ0)) {
             reason = OVF_QUEUE;

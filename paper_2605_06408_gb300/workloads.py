@@ -144,12 +144,13 @@ def power_weights(x: np.ndarray, seed: int = 2, scale: float = 0.2, sigma: float
     return (r * r).astype(np.float32)
 
 
-def gaussian_weights(x: np.ndarray, seed: int = 2) -> np.ndarray:
-    """The paper's power-diagram weights: w ~ N(0, (d_nn^2 / 3)^2), d_nn the
-    median nearest-neighbour distance."""
+def gaussian_weights(x: np.ndarray, seed: int = 2, ratio: float = 1.0 / 3.0) -> np.ndarray:
+    """The paper's power-diagram weights: w ~ N(0, (r d_nn^2)^2), d_nn the
+    median nearest-neighbour distance, r = 1/3 in its main runs (Sec. 5.1)
+    and swept in its weight-distribution ablation."""
     rng = rng_for(seed)
     dnn = float(np.median(nearest_neighbour_distance(x)))
-    return (rng.standard_normal(x.shape[0]) * (dnn * dnn / 3.0)).astype(np.float32)
+    return (rng.standard_normal(x.shape[0]) * (ratio * dnn * dnn)).astype(np.float32)
 
 
 def gradient(n: int, seed: int = 5) -> np.ndarray:
