@@ -116,31 +116,25 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   bool empty = false, overflow = false;
 
   // ---- warm start (App. A.6, with the 32 Morton-order neighbours of the
-  // site instead of a KNN query: one coalesced load, no extra pass)
+  // site instead of a KNN query: one coalesced load, no extra pass): the
+  // window is the first leaf the loop below processes (one inlined copy of
+  // the leaf and clip code serves both)
   int skip0 = 0, skip1 = 0;
-  if (P.cfg.warm_start) {
+  bool warm = P.cfg.warm_start != 0;
+  int cur = SI.root;
+  if (warm) {
     const int lo = SI.first, hi = SI.first + SI.count;
     skip0 = max(lo, min(si - 16, hi - 32));
     skip1 = min(hi, skip0 + 32);
-    int rc = process_leaf(c, S, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, 0, 0);
-    if (rc == CLIP_EMPTY) empty = true;
-    if (rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) {
-      reason = rc == CLIP_OVERFLOW ? OVF_VERTICES : OVF_PLANES;
-      return false;
-    }
-    if (c.dirty) {
-      recompute_aabb(c, S, cull);
-      c.dirty = false;
-    }
+    cur = make_leaf_ref(skip0, skip1 - skip0);
   }
 
   // ---- best-first traversal (Alg. 1)
-  int cur = SI.root;
   bool have = !empty;
   while (!empty) {
     if (have) {
       if (ref_is_leaf(cur)) {
-        int rc = process_leaf(c, S, cur, si, orig_i, P, skip0, skip1);
+        int rc = process_leaf(c, S, cur, si, orig_i, P, warm ? 0 : skip0, warm ? 0 : skip1);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -153,6 +147,11 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
         if (c.dirty) {
           recompute_aabb(c, S, cull);
           c.dirty = false;
+        }
+        if (warm) {  // the warm-start window done: now the traversal from the root
+          warm = false;
+          cur = SI.root;
+          continue;
         }
         have = false;
       } else {

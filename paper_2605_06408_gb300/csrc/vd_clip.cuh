@@ -66,7 +66,6 @@ struct Cell {
   const float* box;  // the set's box: lo[3] then hi[3] (global memory)
   float alo[3], ahi[3];
   float sc[3], srad;  // bounding sphere of the cell (local frame)
-  float em;           // largest vertex error bound
   int nv;
   uint32_t freem[NPW];
   int qn, seq;
@@ -191,7 +190,6 @@ __device__ __forceinline__ void recompute_aabb(Cell<VPL, PCAP, QPL>& c, WarpSmem
       r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
     }
   c.srad = (sqrtf(warp_maxf(r2)) + em) * (1.0f + kCullPad);
-  c.em = em;
   fill_rtab(S.rtab, c.alo, c.ahi, c.sc, c.srad, cull_mode);
 }
 
