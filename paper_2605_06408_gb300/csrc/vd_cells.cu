@@ -85,6 +85,159 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
   return CLIP_NONE;
 }
 
+// Where the outputs of a cell go (cell_outputs).
+struct CellOut {
+  const int* perm;
+  int* counts;
+  float* vol;
+  float* cen;
+  char* tape;
+  const float4* sites;
+  int stride, si, orig_i, setfirst;
+  int* row;
+  float4 me;
+  const float* box;
+  float L;  // largest distance of the cell's AABB corners from the site
+  bool fp64;
+};
+
+// The outputs of a finished cell from its vertices gathered in S (slot
+// order, nv of them, coordinate sums sx, sy, sz, alive planes a0..a3): the
+// neighbour row, the tape record, volume and centroid. Out of line: it runs
+// once per cell, and keeping it out of the traversal loop's code helps the
+// instruction cache. Returns false, writing nothing, if the neighbour list
+// is longer than a row.
+template <int VPL, int PCAP, int QPL>
+static __device__ __noinline__ bool cell_outputs(WarpSmem<VPL, PCAP, QPL>& S, const CellOut O, const int nv,
+                                                 const float sx, const float sy, const float sz, uint32_t a0,
+                                                 uint32_t a1, uint32_t a2, uint32_t a3) {
+  constexpr int NPW = PCAP / 32;
+  const unsigned lane = lane_id(), lt = lanemask_lt();
+  const uint32_t al[4] = {a0, a1, a2, a3};
+  uint32_t alive[NPW];
+#pragma unroll
+  for (int w = 0; w < NPW; w++) alive[w] = al[w];
+  const int si = O.si, orig_i = O.orig_i;
+  int* row = O.row;
+  // neighbours: site planes that carry a face
+  int nvals = 0;
+  const int setfirst = O.setfirst;
+#pragma unroll
+  for (int w = 0; w < NPW; w++) {
+    int f = 32 * w + (int)lane;
+    bool isn = ((alive[w] >> lane) & 1u) && S.pid[f] >= 0;
+    uint32_t mk = __ballot_sync(FULL, isn);
+    if (isn) S.otri[nvals + __popc(mk & lt)] = (uint32_t)(O.perm[S.pid[f]] - setfirst);
+    nvals += __popc(mk);
+  }
+  __syncwarp();
+  if (nvals > O.stride) return false;  // more neighbours than a fast-path row holds
+  for (int t = (int)lane; t < nvals; t += 32) {
+    int v = (int)S.otri[t];
+    int rank = 0;
+    for (int u = 0; u < nvals; u++) rank += (int)S.otri[u] < v;
+    row[rank] = v;
+  }
+  if (O.tape) {
+    // the cell for the adjoint: vertices with plane indices renumbered to
+    // the alive planes' order, and those planes' ids
+    char* rec = O.tape + (size_t)si * kTapeStride;
+    int pre[NPW], nf = 0;
+#pragma unroll
+    for (int w = 0; w < NPW; w++) {
+      pre[w] = nf;
+      nf += __popc(alive[w]);
+    }
+    const bool fits = nv <= kTapeV && nf <= kTapeF;
+    if (fits) {
+      auto rank = [&](uint32_t f) -> uint32_t {
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < NPW; w++)
+          if ((f >> 5) == (uint32_t)w) r = (uint32_t)pre[w] + __popc(alive[w] & ((1u << (f & 31u)) - 1u));
+        return r;
+      };
+      float4* tv = reinterpret_cast<float4*>(rec + kTapeVOff);
+      for (int t = (int)lane; t < nv; t += 32) {
+        const uint32_t T = S.nvt[t];
+        const uint32_t R = rank(T & 255u) | (rank((T >> 8) & 255u) << 8) | (rank((T >> 16) & 255u) << 16);
+        const float4 p = S.nvp[t];
+        tv[t] = make_float4(p.x, p.y, p.z, __uint_as_float(R));
+      }
+      int* tf = reinterpret_cast<int*>(rec + kTapeFOff);
+#pragma unroll
+      for (int w = 0; w < NPW; w++) {
+        const int f = 32 * w + (int)lane;
+        if ((alive[w] >> lane) & 1u) tf[rank((uint32_t)f)] = S.pid[f];
+      }
+    }
+    if (lane == 0) *reinterpret_cast<int4*>(rec) = make_int4(fits ? nv : -1, nf, 0, 0);
+  }
+  // volume and first moment: tetrahedra (c, g_f, v, w) for every directed
+  // edge v -> w of face f (w = the other end of the edge), g_f = the foot of
+  // c on plane f; c = vertex mean
+  float cx = sx / nv, cy = sy / nv, cz = sz / nv;
+  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, Sabs = 0.f, emax = 0.f;
+  for (int it = (int)lane; it < 3 * nv; it += 32) {
+    int t = it / 3, rho = it % 3;
+    uint32_t T = S.nvt[t];
+    uint32_t U = T | (T << 24);
+    uint32_t xy = (U >> (8 * rho)) & 0xffffu;
+    uint32_t fx = xy & 255u, fy = xy >> 8;
+    uint32_t q = fy | (fx << 8);
+    int u = 0;
+    while (u < nv && !tri_has_pair(S.nvt[u], q)) u++;
+    if (u >= nv) continue;  // cannot happen for a closed polytope
+    float4 pf = S.pl[fy];
+    float hgt = fmaf(pf.x, cx, fmaf(pf.y, cy, fmaf(pf.z, cz, -pf.w)));
+    float gx = -hgt * pf.x, gy = -hgt * pf.y, gz = -hgt * pf.z;  // g_f - c
+    float4 a = S.nvp[t], b = S.nvp[u];
+    float ax = a.x - cx, ay = a.y - cy, az = a.z - cz;
+    float bx = b.x - cx, by = b.y - cy, bz = b.z - cz;
+    float det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
+    V += det;
+    Mx += det * (gx + ax + bx);
+    My += det * (gy + ay + by);
+    Mz += det * (gz + az + bz);
+    float e1x = ax - gx, e1y = ay - gy, e1z = az - gz, e2x = bx - gx, e2y = by - gy, e2z = bz - gz;
+    float crx = e1y * e2z - e1z * e2y, cry = e1z * e2x - e1x * e2z, crz = e1x * e2y - e1y * e2x;
+    Sabs += sqrtf(crx * crx + cry * cry + crz * crz);
+    emax = fmaxf(emax, a.w);
+  }
+  V = warp_sumf(V) * (1.0f / 6.0f);
+  Mx = warp_sumf(Mx) * (1.0f / 24.0f);
+  My = warp_sumf(My) * (1.0f / 24.0f);
+  Mz = warp_sumf(Mz) * (1.0f / 24.0f);
+  Sabs = warp_sumf(Sabs) * 0.5f;
+  emax = warp_maxf(emax);
+  const float L = O.L;
+  double ox = cx, oy = cy, oz = cz;
+  double Vd = V;
+  if (O.fp64 && volume_needs_fp64(V, L, Sabs, emax)) {
+    double Mxd, Myd, Mzd;
+    volume_fp64(S, nv, O.me, O.box, O.box + 3, O.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
+    if (Vd > 0.0) {
+      ox += Mxd / Vd;
+      oy += Myd / Vd;
+      oz += Mzd / Vd;
+    }
+    if (lane == 0) S.ct.refvol++;
+  } else if (V > 0.0f) {
+    ox += Mx / V;
+    oy += My / V;
+    oz += Mz / V;
+  }
+  if (lane == 0) {
+    O.counts[orig_i] = nvals;
+    O.vol[orig_i] = (float)Vd;
+    O.cen[3 * (size_t)orig_i] = (float)((double)O.me.x + ox);
+    O.cen[3 * (size_t)orig_i + 1] = (float)((double)O.me.y + oy);
+    O.cen[3 * (size_t)orig_i + 2] = (float)((double)O.me.z + oz);
+  }
+  __syncwarp();
+  return true;
+}
+
 // Build one cell and write its outputs. Returns false on overflow.
 template <int VPL, int PCAP, int QPL>
 __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, int si, int* row, long long& empties,
@@ -216,128 +369,32 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   float sx, sy, sz;
   uint32_t alive[NPW];
   const int nv = gather_vertices(c, S, sx, sy, sz, alive);
-  // neighbours: site planes that carry a face
-  int nvals = 0;
-  const int setfirst = SI.first;
-#pragma unroll
-  for (int w = 0; w < NPW; w++) {
-    int f = 32 * w + (int)lane;
-    bool isn = ((alive[w] >> lane) & 1u) && S.pid[f] >= 0;
-    uint32_t mk = __ballot_sync(FULL, isn);
-    if (isn) S.otri[nvals + __popc(mk & lt)] = (uint32_t)(P.perm[S.pid[f]] - setfirst);
-    nvals += __popc(mk);
-  }
-  __syncwarp();
-  if (nvals > P.stride) {  // more neighbours than a fast-path row holds
-    reason = OVF_NEIGHBORS;
-    return false;
-  }
-  for (int t = (int)lane; t < nvals; t += 32) {
-    int v = (int)S.otri[t];
-    int rank = 0;
-    for (int u = 0; u < nvals; u++) rank += (int)S.otri[u] < v;
-    row[rank] = v;
-  }
-  if (P.tape) {
-    // the cell for the adjoint: vertices with plane indices renumbered to
-    // the alive planes' order, and those planes' ids
-    char* rec = P.tape + (size_t)si * kTapeStride;
-    int pre[NPW], nf = 0;
-#pragma unroll
-    for (int w = 0; w < NPW; w++) {
-      pre[w] = nf;
-      nf += __popc(alive[w]);
-    }
-    const bool fits = nv <= kTapeV && nf <= kTapeF;
-    if (fits) {
-      auto rank = [&](uint32_t f) -> uint32_t {
-        uint32_t r = 0;
-#pragma unroll
-        for (int w = 0; w < NPW; w++)
-          if ((f >> 5) == (uint32_t)w) r = (uint32_t)pre[w] + __popc(alive[w] & ((1u << (f & 31u)) - 1u));
-        return r;
-      };
-      float4* tv = reinterpret_cast<float4*>(rec + kTapeVOff);
-      for (int t = (int)lane; t < nv; t += 32) {
-        const uint32_t T = S.nvt[t];
-        const uint32_t R = rank(T & 255u) | (rank((T >> 8) & 255u) << 8) | (rank((T >> 16) & 255u) << 16);
-        const float4 p = S.nvp[t];
-        tv[t] = make_float4(p.x, p.y, p.z, __uint_as_float(R));
-      }
-      int* tf = reinterpret_cast<int*>(rec + kTapeFOff);
-#pragma unroll
-      for (int w = 0; w < NPW; w++) {
-        const int f = 32 * w + (int)lane;
-        if ((alive[w] >> lane) & 1u) tf[rank((uint32_t)f)] = S.pid[f];
-      }
-    }
-    if (lane == 0) *reinterpret_cast<int4*>(rec) = make_int4(fits ? nv : -1, nf, 0, 0);
-  }
-  // volume and first moment: tetrahedra (c, g_f, v, w) for every directed
-  // edge v -> w of face f (w = the other end of the edge), g_f = the foot of
-  // c on plane f; c = vertex mean
-  float cx = sx / nv, cy = sy / nv, cz = sz / nv;
-  float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, Sabs = 0.f, emax = 0.f;
-  for (int it = (int)lane; it < 3 * nv; it += 32) {
-    int t = it / 3, rho = it % 3;
-    uint32_t T = S.nvt[t];
-    uint32_t U = T | (T << 24);
-    uint32_t xy = (U >> (8 * rho)) & 0xffffu;
-    uint32_t fx = xy & 255u, fy = xy >> 8;
-    uint32_t q = fy | (fx << 8);
-    int u = 0;
-    while (u < nv && !tri_has_pair(S.nvt[u], q)) u++;
-    if (u >= nv) continue;  // cannot happen for a closed polytope
-    float4 pf = S.pl[fy];
-    float hgt = fmaf(pf.x, cx, fmaf(pf.y, cy, fmaf(pf.z, cz, -pf.w)));
-    float gx = -hgt * pf.x, gy = -hgt * pf.y, gz = -hgt * pf.z;  // g_f - c
-    float4 a = S.nvp[t], b = S.nvp[u];
-    float ax = a.x - cx, ay = a.y - cy, az = a.z - cz;
-    float bx = b.x - cx, by = b.y - cy, bz = b.z - cz;
-    float det = gx * (ay * bz - az * by) + gy * (az * bx - ax * bz) + gz * (ax * by - ay * bx);
-    V += det;
-    Mx += det * (gx + ax + bx);
-    My += det * (gy + ay + by);
-    Mz += det * (gz + az + bz);
-    float e1x = ax - gx, e1y = ay - gy, e1z = az - gz, e2x = bx - gx, e2y = by - gy, e2z = bz - gz;
-    float crx = e1y * e2z - e1z * e2y, cry = e1z * e2x - e1x * e2z, crz = e1x * e2y - e1y * e2x;
-    Sabs += sqrtf(crx * crx + cry * cry + crz * crz);
-    emax = fmaxf(emax, a.w);
-  }
-  V = warp_sumf(V) * (1.0f / 6.0f);
-  Mx = warp_sumf(Mx) * (1.0f / 24.0f);
-  My = warp_sumf(My) * (1.0f / 24.0f);
-  Mz = warp_sumf(Mz) * (1.0f / 24.0f);
-  Sabs = warp_sumf(Sabs) * 0.5f;
-  emax = warp_maxf(emax);
   float L = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; k++) L += fmaxf(c.alo[k] * c.alo[k], c.ahi[k] * c.ahi[k]);
-  L = sqrtf(L);
-  double ox = cx, oy = cy, oz = cz;
-  double Vd = V;
-  if (c.fp64 && volume_needs_fp64(V, L, Sabs, emax)) {
-    double Mxd, Myd, Mzd;
-    volume_fp64(S, nv, c.me, c.box, c.box + 3, P.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
-    if (Vd > 0.0) {
-      ox += Mxd / Vd;
-      oy += Myd / Vd;
-      oz += Mzd / Vd;
-    }
-    if (lane == 0) S.ct.refvol++;
-  } else if (V > 0.0f) {
-    ox += Mx / V;
-    oy += My / V;
-    oz += Mz / V;
+  CellOut O;
+  O.perm = P.perm;
+  O.counts = P.counts;
+  O.vol = P.vol;
+  O.cen = P.cen;
+  O.tape = P.tape;
+  O.sites = P.sites;
+  O.stride = P.stride;
+  O.si = si;
+  O.orig_i = orig_i;
+  O.setfirst = SI.first;
+  O.row = row;
+  O.me = c.me;
+  O.box = c.box;
+  O.L = sqrtf(L);
+  O.fp64 = c.fp64;
+  uint32_t al[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int w = 0; w < NPW; w++) al[w] = alive[w];
+  if (!cell_outputs<VPL, PCAP, QPL>(S, O, nv, sx, sy, sz, al[0], al[1], al[2], al[3])) {
+    reason = OVF_NEIGHBORS;
+    return false;
   }
-  if (lane == 0) {
-    P.counts[orig_i] = nvals;
-    vol[orig_i] = (float)Vd;
-    cen[3 * (size_t)orig_i] = (float)((double)c.me.x + ox);
-    cen[3 * (size_t)orig_i + 1] = (float)((double)c.me.y + oy);
-    cen[3 * (size_t)orig_i + 2] = (float)((double)c.me.z + oz);
-  }
-  __syncwarp();
   return true;
 }
 
