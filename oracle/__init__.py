@@ -65,6 +65,8 @@ def _load():
             lib.oracle_cell_vertices.argtypes = [P, P, I64, P, P, I64, C, C, P, P, I32]
             lib.oracle_cell_vertices.restype = C
             lib.oracle_stat_count.restype = C
+            lib.oracle_fd_grad.argtypes = [P, P, I64, P, P, P, P, P, P, P, I64, P, P, P, P, C]
+            lib.oracle_fd_grad.restype = C
             _lib = lib
     return _lib
 
@@ -158,6 +160,30 @@ def grad(xyz, w, bbox, c, d, cells=None, threads=None):
                          _ptr(gp), _ptr(gw), _ptr(st), _threads(threads))
     _check(rc)
     return gp, gw, dict(zip(STAT_NAMES, st.tolist()))
+
+
+def fd_grad(xyz, w, bbox, offsets, nbrs, c, d, sites, hx, hw=None, threads=None):
+    """Central finite differences in FP64 of L = sum_i c_i V_i + d_i . g_i
+    with respect to the positions (and weights) of `sites`, holding the cell
+    combinatorics of the diagram (CSR offsets[n+1], nbrs) fixed; hx / hw are
+    per-site steps. Returns (gp float64[m,3], gw float64[m] or None)."""
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    n = xyz.shape[0]
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64).reshape(n + 1))
+    nb = np.ascontiguousarray(np.asarray(nbrs, dtype=np.int32).reshape(-1))
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(n))
+    d = np.ascontiguousarray(np.asarray(d, dtype=np.float64).reshape(n, 3))
+    idx = np.ascontiguousarray(np.asarray(sites, dtype=np.int64).reshape(-1))
+    m = idx.shape[0]
+    hx = np.ascontiguousarray(np.broadcast_to(np.asarray(hx, dtype=np.float64), (m,)))
+    hwa = None if w is None else np.ascontiguousarray(np.broadcast_to(np.asarray(hw, dtype=np.float64), (m,)))
+    gp = np.zeros((m, 3), np.float64)
+    gw = None if w is None else np.zeros(m, np.float64)
+    rc = lib.oracle_fd_grad(_ptr(xyz), _ptr(w), n, _ptr(lo), _ptr(hi), _ptr(off), _ptr(nb), _ptr(c), _ptr(d),
+                            _ptr(idx), m, _ptr(hx), _ptr(hwa), _ptr(gp), _ptr(gw), _threads(threads))
+    _check(rc)
+    return gp, gw
 
 
 def certify(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, exact=False, threads=None):

@@ -133,7 +133,19 @@ typedef struct {
    * index): their cells are empty and their half-spaces are implied by the
    * winner's, so they are never candidates */
   unsigned char* dup_loser;
+  /* finite differences: site ov_site at (ov_xyz, ov_w) in FP64 instead of
+   * its float32 input (-1: none) */
+  int64_t ov_site;
+  double ov_xyz[3];
+  double ov_w;
 } problem_t;
+
+static double site_x(const problem_t* pr, int64_t i, int k) {
+  return i == pr->ov_site ? pr->ov_xyz[k] : (double)pr->xyz[3 * i + k];
+}
+static double site_w(const problem_t* pr, int64_t i) {
+  return i == pr->ov_site ? pr->ov_w : (pr->w ? (double)pr->w[i] : 0.0);
+}
 
 static double dmax(double a, double b) { return a > b ? a : b; }
 
@@ -188,11 +200,11 @@ static int add_plane(cell_t* C, const plane_t* P) {
 
 /* site plane of j for cell i, local coordinates around p_i */
 static void make_site_plane(const problem_t* pr, int64_t i, int64_t j, plane_t* P) {
-  double wi = pr->w ? (double)pr->w[i] : 0.0;
-  double wj = pr->w ? (double)pr->w[j] : 0.0;
+  double wi = site_w(pr, i);
+  double wj = site_w(pr, j);
   double nn = 0.0;
   for (int k = 0; k < 3; k++) {
-    P->n[k] = (double)pr->xyz[3 * j + k] - (double)pr->xyz[3 * i + k];
+    P->n[k] = site_x(pr, j, k) - site_x(pr, i, k);
     nn += P->n[k] * P->n[k];
   }
   P->b = 0.5 * (nn + (wi - wj));
@@ -213,7 +225,7 @@ static void make_site_plane(const problem_t* pr, int64_t i, int64_t j, plane_t* 
 static void make_box_plane(const problem_t* pr, int64_t i, int k, plane_t* P) {
   int ax = k >> 1;
   double s = (k & 1) ? -1.0 : 1.0;
-  double pi = (double)pr->xyz[3 * i + ax];
+  double pi = site_x(pr, i, ax);
   P->n[0] = P->n[1] = P->n[2] = 0.0;
   P->n[ax] = s;
   P->b = (k & 1) ? (pi - pr->lo[ax]) : (pr->hi[ax] - pi);
@@ -931,6 +943,7 @@ static void free_problem(problem_t* pr) {
 static int setup_problem(problem_t* pr, const float* xyz, const float* w, int64_t n, const float* lo,
                          const float* hi, int exact) {
   memset(pr, 0, sizeof(*pr));
+  pr->ov_site = -1;
   pr->xyz = xyz;
   pr->w = w;
   pr->n = n;
@@ -1424,6 +1437,118 @@ int oracle_cell_vertices(const float* xyz, const float* w, int64_t n, const floa
   if (mode == 1) kd_free(&T);
   free_problem(&pr);
   return out;
+}
+
+/* Cell i as the box clipped by the planes of its neighbour row only (the
+ * combinatorics held fixed); its volume and first moment about p_i. */
+static int fd_cell(const problem_t* pr, int64_t i, const int64_t* offsets, const int32_t* nbrs, cell_t* C,
+                   int* poly, int cap, int64_t* stats, double* V, double mom[3]) {
+  cell_start(pr, i, C);
+  for (int64_t e = offsets[i]; e < offsets[i + 1] && !C->empty; e++) {
+    plane_t P;
+    make_site_plane(pr, i, (int64_t)nbrs[e], &P);
+    int r = cell_clip(pr, C, &P, stats);
+    if (r < 0) return r;
+  }
+  *V = 0.0;
+  mom[0] = mom[1] = mom[2] = 0.0;
+  if (C->empty || C->nv == 0) return 0;
+  return cell_volume(C, V, mom, poly, cap, stats);
+}
+
+/*
+ * oracle_fd_grad: central finite differences of L = sum_i c_i V_i + d_i . g_i
+ * (V_i volume, g_i centroid) with respect to the coordinates and the weight
+ * of each listed site, with the cell combinatorics held fixed as in the
+ * analytic gradient: moving site k moves only faces of cell k and of its
+ * neighbours' cells, so L changes only through those cells; each is rebuilt,
+ * with site k moved in FP64, as the box clipped by the planes of its own
+ * neighbour row of the unperturbed diagram. A cell with an empty row is an
+ * empty cell and contributes nothing (its gradient is 0 by the convention of
+ * the analytic gradient, although its reported centroid is its site).
+ *   offsets [n+1] int64, nbrs int32: the diagram's CSR over all n sites.
+ *   c [n], d [3n] float64: the loss coefficients.
+ *   sites [m] int64; hx [m] position steps, hw [m] weight steps (absolute;
+ *   hw unused without weights).
+ *   gp [3m] and gw [m] (NULL without weights) float64 out.
+ * Returns 0 or a negative error code.
+ */
+int oracle_fd_grad(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi,
+                   const int64_t* offsets, const int32_t* nbrs, const double* c, const double* d,
+                   const int64_t* sites, int64_t m, const double* hx, const double* hw, double* gp, double* gw,
+                   int nthreads) {
+  if (n <= 0 || !xyz || !offsets || !nbrs || !c || !d || !sites || !hx || !gp || (w && (!hw || !gw)))
+    return ORC_ERR_ARG;
+  problem_t base;
+  int rc = setup_problem(&base, xyz, w, n, lo, hi, 0);
+  if (rc) {
+    free_problem(&base);
+    return rc;
+  }
+  int err = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel
+  {
+    problem_t pr = base;
+    cell_t C;
+    cell_init_storage(&C);
+    int cap = 4096;
+    int* poly = (int*)xrealloc(NULL, sizeof(int) * cap);
+    int64_t st[ST_N];
+    for (int k = 0; k < ST_N; k++) st[k] = 0;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < m; q++) {
+      const int64_t k = sites[q];
+      if (k < 0 || k >= n) {
+#pragma omp atomic write
+        err = ORC_ERR_ARG;
+        continue;
+      }
+      const int nparam = w ? 4 : 3;
+      for (int a = 0; a < nparam; a++) {
+        const double h = a < 3 ? hx[q] : hw[q];
+        double Ls[2] = {0.0, 0.0};
+        for (int s = 0; s < 2; s++) {
+          pr.ov_site = k;
+          for (int t = 0; t < 3; t++) pr.ov_xyz[t] = (double)xyz[3 * k + t];
+          pr.ov_w = w ? (double)w[k] : 0.0;
+          if (a < 3)
+            pr.ov_xyz[a] += s ? -h : h;
+          else
+            pr.ov_w += s ? -h : h;
+          double L = 0.0;
+          for (int64_t e = offsets[k] - 1; e < offsets[k + 1]; e++) {
+            const int64_t i = e < offsets[k] ? k : (int64_t)nbrs[e];
+            if (offsets[i + 1] == offsets[i]) continue; /* an empty cell: gradient 0 by convention */
+            double V, mom[3];
+            int r = fd_cell(&pr, i, offsets, nbrs, &C, poly, cap, st, &V, mom);
+            if (r < 0) {
+#pragma omp atomic write
+              err = r;
+              break;
+            }
+            double g[3];
+            for (int t = 0; t < 3; t++) g[t] = site_x(&pr, i, t) + (V > 0.0 ? mom[t] / V : 0.0);
+            L += c[i] * V + d[3 * i] * g[0] + d[3 * i + 1] * g[1] + d[3 * i + 2] * g[2];
+          }
+          Ls[s] = L;
+        }
+        const double g = (Ls[0] - Ls[1]) / (2.0 * h);
+        if (a < 3)
+          gp[3 * q + a] = g;
+        else
+          gw[q] = g;
+      }
+    }
+    free(poly);
+    cell_free_storage(&C);
+  }
+  free_problem(&base);
+  return err;
 }
 
 int oracle_stat_count(void) { return ST_N; }

@@ -1,7 +1,8 @@
 """Full-size configurations through the C ABI, checked on sampled cells
 against the FP64 oracle: the batched build (256 sets, ~9M sites) eager and
 replayed from a CUDA graph, the adjoint at 1M sites, and the 20M-site
-surface set (forward + adjoint)."""
+surface set (forward + adjoint; the adjoint also against FP64 central finite
+differences on 1,000 sites)."""
 import numpy as np
 import pytest
 
@@ -120,3 +121,20 @@ def test_surfaces_20M_forward_and_backward(vdmod):
     c, d = W.loss_coefficients(len(x), 4)
     gp, _ = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=False)
     _grad_subset_check(x, None, res, gp, None, c, d, k=150, seed=12)
+    # FP64 central finite differences on 1,000 sites, combinatorics from the
+    # oracle's own neighbour rows of those sites and their neighbours
+    K = np.sort(W.rng_for(13).choice(len(x), 1000, replace=False))
+    rk = oracle.cells(x, None, W.UNIT_BOX, cells=K)
+    A = np.unique(np.concatenate([K] + list(rk["nbrs"]))).astype(np.int64)
+    ra = oracle.cells(x, None, W.UNIT_BOX, cells=A)
+    counts = np.zeros(len(x), np.int64)
+    counts[A] = [len(v) for v in ra["nbrs"]]
+    off = np.concatenate([[0], np.cumsum(counts)])
+    nb = np.concatenate(ra["nbrs"]).astype(np.int32)  # rows of A in ascending site order = CSR order
+    pos = {int(s): q for q, s in enumerate(A)}
+    h = np.array([1e-4 * np.min(np.linalg.norm(x[ra["nbrs"][pos[int(k)]]].astype(np.float64) - x[k], axis=1))
+                  for k in K])
+    fd, _ = oracle.fd_grad(x, None, W.UNIT_BOX, off, nb, c, d, K, hx=h)
+    g = gp.cpu().numpy()[K].astype(np.float64)
+    err = np.abs(g - fd).max(1) / np.maximum(np.abs(fd).max(1), 1e-30)
+    assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())

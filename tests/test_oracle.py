@@ -293,3 +293,37 @@ def test_gradient_subset_matches_full():
     gps, gws, _ = oracle.grad(x, None, BOX, c, d, cells=sub)
     np.testing.assert_allclose(gps[k], gp[k], rtol=1e-12, atol=1e-15)
     assert gws[k] == pytest.approx(gw[k], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_fd_grad_matches_analytic_and_full_rebuild(weighted):
+    """oracle.fd_grad (central differences in FP64, each affected cell
+    rebuilt from its neighbour row) agrees with the Reynolds-transport
+    gradient and with differences of full rebuilds (float32 steps)."""
+    n = 150
+    x = W.uniform(n, 71)
+    w = W.power_weights(x, 72, scale=0.5) if weighted else None
+    c, d = W.loss_coefficients(n, 73)
+    r = oracle.cells(x, w)
+    off = np.concatenate([[0], np.cumsum([len(v) for v in r["nbrs"]])]).astype(np.int64)
+    nb = np.concatenate(r["nbrs"]).astype(np.int32)
+    sites = np.arange(n, dtype=np.int64)
+    gp_fd, gw_fd = oracle.fd_grad(x, w, BOX, off, nb, c, d, sites, hx=1e-7, hw=1e-9)
+    gp, gw, _ = oracle.grad(x, w, BOX, c, d)
+    scale = np.abs(gp).max()
+    np.testing.assert_allclose(gp_fd, gp, rtol=1e-6, atol=1e-7 * scale)
+    if weighted:
+        np.testing.assert_allclose(gw_fd, gw, rtol=1e-5, atol=1e-6 * np.abs(gw).max())
+    # against full rebuilds with float32 steps where the combinatorics hold
+    # (non-empty cells: an empty cell reports its site as centroid)
+    for k in [q for q in range(n) if r["vol"][q] > 0][:3]:
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[k, a] = np.float32(x[k, a] + 2.0 ** -16)
+            xm[k, a] = np.float32(x[k, a] - 2.0 ** -16)
+            Lp, nbp = _loss(xp, w, c, d)
+            Lm, nbm = _loss(xm, w, c, d)
+            if not all(np.array_equal(u, v) for u, v in zip(nbp, nbm)):
+                continue
+            fd = (Lp - Lm) / (float(xp[k, a]) - float(xm[k, a]))
+            assert fd == pytest.approx(gp_fd[k, a], rel=2e-5, abs=2e-6)
