@@ -58,7 +58,7 @@ WORKLOADS = {
                   "per step, replayed from a CUDA graph",
 }
 
-# algorithmic FP32 work per counted event ("Roofline"):
+# algorithmic FP32 work per counted event:
 # one vertex/plane sign test = 3 FMA; one new vertex = three cross products,
 # a determinant, three 3-term numerators and a reciprocal (51 flop); one leaf
 # candidate = its plane and support test (30 flop); one BVH child = its
