@@ -100,3 +100,24 @@ def test_autotune_batched(vdmod):
     cfg = ctx.autotune_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k], max_trials=6)
     assert cfg["cell_mode"] in (0, 1)
     same_cells(ctx.build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k]), ref)
+
+
+@pytest.mark.parametrize("cell_mode", [0, 1])
+def test_batched_adjoint_with_tape(vdmod, cell_mode):
+    """Adjoint of a batched build: from the tape (warp form) or re-clipped
+    (the thread form keeps no tape) -- both equal to full recomputation."""
+    X, Wt, offs, flags = W.batched(3)
+    k = 12
+    n = int(offs[k])
+    boxes = [W.UNIT_BOX] * k
+    ctx = vdmod.Context(0, {"tape": 1, "cell_mode": cell_mode})
+    ctx.build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
+    c, d = W.loss_coefficients(n, 5)
+    gv, gc = dev(c.astype(np.float32)), dev(d.astype(np.float32))
+    gp_t, gw_t = ctx.backward(gv, gc, want_weights=True)
+    gp_r, gw_r = ctx.backward(gv, gc, want_weights=True, recompute=True)
+    scale = gp_r.abs().max(dim=1).values.clamp_min(1e-30)
+    rel = (gp_t - gp_r).abs().max(dim=1).values / scale
+    assert rel.quantile(0.999).item() < 1e-3 and rel.max().item() < 0.05
+    if cell_mode == 1:  # no tape: the same computation
+        assert torch.equal(gp_t, gp_r)
