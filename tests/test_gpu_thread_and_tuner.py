@@ -119,5 +119,5 @@ def test_batched_adjoint_with_tape(vdmod, cell_mode):
     scale = gp_r.abs().max(dim=1).values.clamp_min(1e-30)
     rel = (gp_t - gp_r).abs().max(dim=1).values / scale
     assert rel.quantile(0.999).item() < 1e-3 and rel.max().item() < 0.05
-    if cell_mode == 1:  # no tape: the same computation
-        assert torch.equal(gp_t, gp_r)
+    if cell_mode == 1:  # no tape: the same computation (up to the order of the atomic sums)
+        assert torch.allclose(gp_t, gp_r, rtol=1e-5, atol=1e-6 * gp_r.abs().max().item())
