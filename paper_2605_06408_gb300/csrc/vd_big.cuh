@@ -512,8 +512,8 @@ struct HelpBoard {
   HelpReq req[kBigWarpsPerBlock];
   int live;  // warps of the block still building their own cells
 };
-constexpr int kHelpMinChunks = 64;  // filters over fewer chunks run alone
-constexpr int kHelpGroup = 16;      // chunks per claim
+constexpr int kHelpMinChunks = 32;  // filters over fewer chunks run alone
+constexpr int kHelpGroup = 8;       // chunks per claim
 constexpr long long kWaitLimit = 1ll << 24;
 
 __device__ __forceinline__ int vload(const int* p) { return *(const volatile int*)p; }
