@@ -248,6 +248,42 @@ int vd_get_status(vd_ctx* ctx, vd_status* st);
 /* Static string for a VD_* code (never NULL). */
 const char* vd_error_string(int code);
 
+/* ---- explicit mesh output and vertex gradients (no paper counterpart: the
+ * paper outputs the connectivity; the cell vertices are the mesh a
+ * Voronoi-based renderer needs, and their gradients the adjoint's third
+ * input) --------------------------------------------------------------- */
+typedef struct {
+  int32_t* vertex_offsets; /* [n+1] DEVICE: vertices of cell i are rows            */
+                           /*   vertex_offsets[i] .. vertex_offsets[i+1]-1         */
+  float* vertices;         /* [3 capacity] DEVICE: world positions                 */
+  int32_t* vertex_sites;   /* [3 capacity] DEVICE: the other three sites whose     */
+                           /*   planes meet at the vertex (indices in the cell's   */
+                           /*   set), or -1-f for box face f (0:+x 1:-x 2:+y 3:-y  */
+                           /*   4:+z 5:-z)                                         */
+  int64_t capacity;        /* vertices that fit (0: counts and offsets only)       */
+  int64_t* nverts_out;     /* DEVICE scalar: total vertex count (always written)   */
+  int32_t* status;         /* DEVICE scalar or NULL: VD_OK, or VD_ERR_CAPACITY     */
+} vd_mesh;
+
+/* vd_cells_mesh: the vertices of every cell of the last build, in the order
+ * vd_backward_mesh expects their gradients (cells from the forward's tape
+ * when it kept one, else re-clipped from the CSR; empty cells have none).
+ * Asynchronous on `stream`; a cell whose rows do not fit `capacity` is not
+ * written and sets VD_ERR_CAPACITY (nverts_out holds the size to allocate).
+ * Errors: VD_ERR_INVALID_ARG, VD_ERR_NO_FORWARD, VD_ERR_CUDA. */
+int vd_cells_mesh(vd_ctx* ctx, const vd_mesh* out, void* stream);
+
+/* vd_backward_mesh: vd_backward(recompute = 0) plus the gradient of L with
+ * respect to every cell vertex: grad_vertices [3 V] DEVICE float32 in the
+ * order of vd_cells_mesh of the same build (vertex_offsets its offsets), or
+ * NULL. Each vertex is the solution of the 3x3 system of the planes that
+ * meet there; its gradient reaches the four sites (and weights) of those
+ * planes by implicit differentiation, box faces being fixed.
+ * Errors: as vd_backward; VD_ERR_INVALID_ARG if grad_vertices is given
+ * without vertex_offsets. */
+int vd_backward_mesh(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, const float* grad_vertices,
+                     const int32_t* vertex_offsets, float* grad_sites, float* grad_weights, void* stream);
+
 /* ---- autotuner (a project addition: the paper has no tuner; its kernel
  * capacities are fixed per build) ------------------------------------------
  *

@@ -214,3 +214,44 @@ def cell_vertices(xyz, w, bbox, i, mode="kd", exact=False, cap=4096):
     if k < 0:
         _check(k)
     return pos[:k].copy(), tri[:k].copy()
+
+
+def vertex_grad(xyz, w, bbox, cells, gfun, threads=None):
+    """Gradient, with respect to the site positions and weights, of
+    L = sum over the listed cells i and their vertices x of gfun(i, sites) . x,
+    the cell combinatorics held fixed. `sites` is the vertex's triple of
+    other defining sites (-1-f for box face f, as cell_vertices gives them);
+    gfun returns a float64[3]. Each vertex solves A x = r with the rows
+    2 (p_j - p_i) . x = |p_j|^2 - |p_i|^2 + w_i - w_j of its site planes and
+    +-x_axis = bound of its box faces; with lambda = A^-T g, implicit
+    differentiation gives dL/dp_j = 2 lambda_j (p_j - x), dL/dw_j = -lambda_j,
+    dL/dp_i += 2 lambda_j (x - p_i), dL/dw_i += lambda_j. Plain FP64 numpy
+    over the oracle's own vertices. Returns (gp float64[n,3], gw float64[n])."""
+    x = np.asarray(xyz, dtype=np.float32).reshape(-1, 3)
+    wt = None if w is None else np.asarray(w, dtype=np.float32).reshape(-1)
+    n = x.shape[0]
+    gp = np.zeros((n, 3), np.float64)
+    gw = np.zeros(n, np.float64)
+    P = x.astype(np.float64)
+    for i in np.asarray(cells, dtype=np.int64).reshape(-1):
+        pos, tri = cell_vertices(x, wt, bbox, int(i))
+        pi = P[i]
+        for v, t in zip(pos, tri):
+            X = pi + v
+            g = np.asarray(gfun(int(i), tuple(int(s) for s in t)), dtype=np.float64)
+            A = np.zeros((3, 3))
+            for k, s in enumerate(t):
+                if s >= 0:
+                    A[k] = 2.0 * (P[s] - pi)
+                else:
+                    f = -1 - s
+                    A[k, f >> 1] = -1.0 if (f & 1) else 1.0
+            lam = np.linalg.solve(A.T, g)
+            for k, s in enumerate(t):
+                if s < 0:
+                    continue
+                gp[s] += 2.0 * lam[k] * (P[s] - X)
+                gp[i] += 2.0 * lam[k] * (X - pi)
+                gw[s] -= lam[k]
+                gw[i] += lam[k]
+    return gp, gw

@@ -71,6 +71,7 @@ struct vd_ctx {
   int* ovf_list = nullptr;
   int* ovf_slot = nullptr;
   int* blist = nullptr;
+  int* vcount = nullptr;  // mesh output: vertices per cell
   long long* block_sums = nullptr;
   int* work = nullptr;  // [8] work counters
   unsigned* wrange = nullptr;  // [2] orderable min / max weight
@@ -176,6 +177,7 @@ static Layout make_layout(int64_t n, int num_sms) {
   L.add(sizeof(SetInfo) * kMaxSets);   // 24 sets
   L.add(big_arena_bytes() * (size_t)big_warps(num_sms));  // 25 arenas
   L.add((size_t)n);                    // 26 duplicate losers
+  L.add(sizeof(int) * n);              // 27 mesh vertex count per cell
   return L;
 }
 
@@ -240,6 +242,7 @@ static int reserve(vd_ctx* ctx, int64_t n) {
   ctx->pool_cap = pool_capacity(want);
   ctx->arena = b + L.off[25];
   ctx->loser = (unsigned char*)(b + L.off[26]);
+  ctx->vcount = (int*)(b + L.off[27]);
   ctx->ovf_list = (int*)(b + L.off[18]);
   ctx->ovf_slot = (int*)(b + L.off[19]);
   ctx->blist = (int*)(b + L.off[20]);
@@ -527,38 +530,99 @@ int vd_build_batched(vd_ctx* ctx, const float* xyz, const float* weights, const 
   return run_forward(ctx, xyz, weights, (int)n, nsets, 54, out, (cudaStream_t)stream);
 }
 
-int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
-                float* grad_weights, int recompute, void* stream) {
-  if (!ctx || !grad_sites || (recompute != 0 && recompute != 1)) return VD_ERR_INVALID_ARG;
-  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
-  cudaStream_t s = (cudaStream_t)stream;
-  int n = ctx->last_n;
-  cudaMemsetAsync(grad_sites, 0, sizeof(float) * 3 * (size_t)n, s);
-  if (grad_weights) cudaMemsetAsync(grad_weights, 0, sizeof(float) * (size_t)n, s);
+}  // extern "C"
+
+// One pass of the adjoint kernels over the last build's cells: gradients
+// (mode 0), mesh vertex counts (1) or mesh output (2).
+static int back_pass(vd_ctx* ctx, BackBuffers b, cudaStream_t s) {
   cudaMemsetAsync(ctx->work + 2, 0, sizeof(int) * 3, s);
-  cudaMemsetAsync(&ctx->st->error, 0, sizeof(int), s);
-  BackBuffers b;
   b.c = cell_buffers(ctx);
   b.inv_perm = ctx->inv_perm;
-  b.gvol = grad_volume;
-  b.gcen = grad_centroid;
-  b.gp = grad_sites;
-  b.gw = grad_weights;
   b.list = ctx->blist;
   b.list_count = ctx->work + 4;
   b.list_cap = ctx->ovf_cap;
   b.work = ctx->work + 2;
+  return cuda_fail(launch_backward(b, ctx->num_sms, s));
+}
+
+static int backward_common(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid,
+                           const float* grad_vertices, const int32_t* vertex_offsets, float* grad_sites,
+                           float* grad_weights, int recompute, cudaStream_t s) {
+  int n = ctx->last_n;
+  cudaMemsetAsync(grad_sites, 0, sizeof(float) * 3 * (size_t)n, s);
+  if (grad_weights) cudaMemsetAsync(grad_weights, 0, sizeof(float) * (size_t)n, s);
+  cudaMemsetAsync(&ctx->st->error, 0, sizeof(int), s);
+  BackBuffers b;
+  std::memset(&b, 0, sizeof(b));
+  b.gvol = grad_volume;
+  b.gcen = grad_centroid;
+  b.gp = grad_sites;
+  b.gw = grad_weights;
   b.tape = (recompute == 0 && ctx->tape_valid) ? ctx->tape : nullptr;
+  b.mode = 0;
+  b.gvert = grad_vertices;
+  b.voff = vertex_offsets;
   ctx->ev_valid = false;
   mark(ctx, 0, s);
-  cudaError_t e = launch_backward(b, ctx->num_sms, s);
+  int rc = back_pass(ctx, b, s);
   mark(ctx, 6, s);
   ctx->last_stream = s;
   ctx->ev_valid = ctx->cfg.timing != 0;
   ctx->ev_backward = true;
   ctx->launches = 2;
-  return cuda_fail(e);
+  return rc;
+}
+
+extern "C" {
+
+int vd_backward(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, float* grad_sites,
+                float* grad_weights, int recompute, void* stream) {
+  if (!ctx || !grad_sites || (recompute != 0 && recompute != 1)) return VD_ERR_INVALID_ARG;
+  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  return backward_common(ctx, grad_volume, grad_centroid, nullptr, nullptr, grad_sites, grad_weights, recompute,
+                         (cudaStream_t)stream);
+}
+
+int vd_cells_mesh(vd_ctx* ctx, const vd_mesh* out, void* stream) {
+  if (!ctx || !out || !out->vertex_offsets || !out->nverts_out || out->capacity < 0) return VD_ERR_INVALID_ARG;
+  if (out->capacity > 0 && (!out->vertices || !out->vertex_sites)) return VD_ERR_INVALID_ARG;
+  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = ctx->last_n;
+  cudaMemsetAsync(&ctx->st->error, 0, sizeof(int), s);
+  cudaMemsetAsync(ctx->vcount, 0, sizeof(int) * (size_t)n, s);
+  BackBuffers b;
+  std::memset(&b, 0, sizeof(b));
+  b.tape = ctx->tape_valid ? ctx->tape : nullptr;  // the cells vd_backward(recompute = 0) uses
+  b.mode = 1;
+  b.vcount = ctx->vcount;
+  int rc = back_pass(ctx, b, s);
+  if (rc) return rc;
+  if (launch_scan(ctx->vcount, n, out->vertex_offsets, ctx->block_sums, &ctx->st->nverts, ctx->st, s) !=
+      cudaSuccess)
+    return VD_ERR_CUDA;
+  if (out->capacity > 0) {
+    b.mode = 2;
+    b.voff = out->vertex_offsets;
+    b.vout = out->vertices;
+    b.vsites = out->vertex_sites;
+    b.vcap = out->capacity;
+    rc = back_pass(ctx, b, s);
+    if (rc) return rc;
+  }
+  ctx->last_stream = s;
+  return cuda_fail(launch_mesh_finish(ctx->st, out->nverts_out, out->status, s));
+}
+
+int vd_backward_mesh(vd_ctx* ctx, const float* grad_volume, const float* grad_centroid, const float* grad_vertices,
+                     const int32_t* vertex_offsets, float* grad_sites, float* grad_weights, void* stream) {
+  if (!ctx || !grad_sites || (grad_vertices && !vertex_offsets)) return VD_ERR_INVALID_ARG;
+  if (!ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  return backward_common(ctx, grad_volume, grad_centroid, grad_vertices, vertex_offsets, grad_sites, grad_weights,
+                         0, (cudaStream_t)stream);
 }
 
 int vd_get_timings(vd_ctx* ctx, vd_timings* t) {

@@ -82,6 +82,73 @@ __device__ __forceinline__ void face_accumulate(float* A, const float* g, const 
   }
 }
 
+// Row of the plane through a vertex in the linear system A x = r that
+// defines it (world coordinates): a site plane j of cell i is
+// 2 (p_j - p_i) . x = |p_j|^2 - |p_i|^2 + w_i - w_j; box face f is
+// +-x_axis = bound. nj = p_j - p_i (site) or unused (box).
+__device__ __forceinline__ void plane_row(int id, float nx, float ny, float nz, float r[3]) {
+  if (id >= 0) {
+    r[0] = 2.0f * nx;
+    r[1] = 2.0f * ny;
+    r[2] = 2.0f * nz;
+  } else {
+    const int f = -1 - id, ax = f >> 1;
+    const float sg = (f & 1) ? -1.0f : 1.0f;
+    r[0] = ax == 0 ? sg : 0.0f;
+    r[1] = ax == 1 ? sg : 0.0f;
+    r[2] = ax == 2 ? sg : 0.0f;
+  }
+}
+
+// Adjoint of one vertex x (local position v = x - p_i) of cell i defined by
+// the planes of ids[0..2]: with lambda = A^-T g (g = dL/dx), implicit
+// differentiation of A x = r gives dL/dp_j = 2 lambda_j (p_j - x),
+// dL/dw_j = -lambda_j for each site plane j, and dL/dp_i += 2 lambda_j
+// (x - p_i), dL/dw_i += lambda_j; box faces do not move.
+__device__ __forceinline__ void vertex_gradient(const float4* __restrict__ sites, const int* __restrict__ perm,
+                                                float4 me, float4 v, const int ids[3], float g0, float g1, float g2,
+                                                float* gp, float* gw, float& gpi0, float& gpi1, float& gpi2,
+                                                float& gwi) {
+  float n[3][3], r[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    n[k][0] = n[k][1] = n[k][2] = 0.0f;
+    if (ids[k] >= 0) {
+      const float4 q = sites[ids[k]];
+      n[k][0] = q.x - me.x;
+      n[k][1] = q.y - me.y;
+      n[k][2] = q.z - me.z;
+    }
+    plane_row(ids[k], n[k][0], n[k][1], n[k][2], r[k]);
+  }
+  float cr[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float* a = r[(k + 1) % 3];
+    const float* b = r[(k + 2) % 3];
+    cr[k][0] = a[1] * b[2] - a[2] * b[1];
+    cr[k][1] = a[2] * b[0] - a[0] * b[2];
+    cr[k][2] = a[0] * b[1] - a[1] * b[0];
+  }
+  const float det = r[0][0] * cr[0][0] + r[0][1] * cr[0][1] + r[0][2] * cr[0][2];
+  if (!(fabsf(det) > 0.0f)) return;
+  const float idet = 1.0f / det;
+  const float vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    if (ids[k] < 0) continue;
+    const float lam = (cr[k][0] * g0 + cr[k][1] * g1 + cr[k][2] * g2) * idet;
+    const int oj = perm[ids[k]];
+#pragma unroll
+    for (int p = 0; p < 3; p++) atomicAdd(&gp[3 * (size_t)oj + p], 2.0f * lam * (n[k][p] - vv[p]));
+    if (gw) atomicAdd(&gw[oj], -lam);
+    gpi0 += 2.0f * lam * vv[0];
+    gpi1 += 2.0f * lam * vv[1];
+    gpi2 += 2.0f * lam * vv[2];
+    gwi += lam;
+  }
+}
+
 template <int VPL, int PCAP, int QPL>
 __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si) {
   using C = Cell<VPL, PCAP, QPL>;
@@ -179,6 +246,30 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
   }
   nv = gather_vertices(c, S, sx, sy, sz, alive);
   }
+  if (B.mode == 1) {  // vertex count of the mesh output
+    if (lane == 0) B.vcount[orig_i] = nv;
+    return true;
+  }
+  if (B.mode == 2) {  // the mesh output: world positions and defining sites
+    const long long base = B.voff[orig_i];
+    if (base + nv > B.vcap) {
+      if (lane == 0) set_error(P.st, VD_ERR_CAPACITY);
+      return true;
+    }
+    for (int t = (int)lane; t < nv; t += 32) {
+      const float4 v = S.nvp[t];
+      const uint32_t T = S.nvt[t];
+      B.vout[3 * (base + t)] = c.me.x + v.x;
+      B.vout[3 * (base + t) + 1] = c.me.y + v.y;
+      B.vout[3 * (base + t) + 2] = c.me.z + v.z;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const int id = S.pid[(T >> (8 * k)) & 255u];
+        B.vsites[3 * (base + t) + k] = id >= 0 ? P.perm[id] - SI.first : id;
+      }
+    }
+    return true;
+  }
   const float cx = sx / nv, cy = sy / nv, cz = sz / nv;
   for (int f = (int)lane; f < PCAP; f += 32)
 #pragma unroll
@@ -235,6 +326,17 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
     int js = S.pid[f];
     face_gradient(SM.acc[f], cx, cy, cz, c.me, P.sites[js], P.perm[js], ap, b0, b1, b2, B.gp, B.gw, gpi0, gpi1,
                   gpi2, gwi);
+  }
+  if (B.gvert) {  // gradients of the cell's vertices (mesh order)
+    const long long base = B.voff[orig_i];
+    for (int t = (int)lane; t < nv; t += 32) {
+      const float* g = B.gvert + 3 * (base + t);
+      const float g0 = g[0], g1 = g[1], g2 = g[2];
+      if (g0 == 0.0f && g1 == 0.0f && g2 == 0.0f) continue;
+      const uint32_t T = S.nvt[t];
+      const int ids[3] = {S.pid[T & 255u], S.pid[(T >> 8) & 255u], S.pid[(T >> 16) & 255u]};
+      vertex_gradient(P.sites, P.perm, c.me, S.nvp[t], ids, g0, g1, g2, B.gp, B.gw, gpi0, gpi1, gpi2, gwi);
+    }
   }
   gpi0 = warp_sumf(gpi0);
   gpi1 = warp_sumf(gpi1);
@@ -345,6 +447,30 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
     }
   }
   big_compact(c, A);
+  if (B.mode == 1) {
+    if (lane == 0) B.vcount[orig_i] = c.nv;
+    return true;
+  }
+  if (B.mode == 2) {
+    const long long base = B.voff[orig_i];
+    if (base + c.nv > B.vcap) {
+      if (lane == 0) set_error(P.st, VD_ERR_CAPACITY);
+      return true;
+    }
+    for (int t = (int)lane; t < c.nv; t += 32) {
+      const float4 v = A.vp[t];
+      const uint64_t T = A.vt[t];
+      B.vout[3 * (base + t)] = c.me.x + v.x;
+      B.vout[3 * (base + t) + 1] = c.me.y + v.y;
+      B.vout[3 * (base + t) + 2] = c.me.z + v.z;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const int id = A.pid[bfield(T, k)];
+        B.vsites[3 * (base + t) + k] = id >= 0 ? P.perm[id] - SI.first : id;
+      }
+    }
+    return true;
+  }
   big_mark_planes(c, A);
   const uint32_t hmask = big_hash_vertices(c, A);
   float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -401,6 +527,17 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
     int js = A.pid[f];
     face_gradient(A.acc + 10 * (size_t)f, cx, cy, cz, c.me, P.sites[js], P.perm[js], ap, b0, b1, b2, B.gp, B.gw,
                   gpi0, gpi1, gpi2, gwi);
+  }
+  if (B.gvert) {  // gradients of the cell's vertices (mesh order)
+    const long long base = B.voff[orig_i];
+    for (int t = (int)lane; t < c.nv; t += 32) {
+      const float* g = B.gvert + 3 * (base + t);
+      const float g0 = g[0], g1 = g[1], g2 = g[2];
+      if (g0 == 0.0f && g1 == 0.0f && g2 == 0.0f) continue;
+      const uint64_t T = A.vt[t];
+      const int ids[3] = {A.pid[bfield(T, 0)], A.pid[bfield(T, 1)], A.pid[bfield(T, 2)]};
+      vertex_gradient(P.sites, P.perm, c.me, A.vp[t], ids, g0, g1, g2, B.gp, B.gw, gpi0, gpi1, gpi2, gwi);
+    }
   }
   gpi0 = warp_sumf(gpi0);
   gpi1 = warp_sumf(gpi1);

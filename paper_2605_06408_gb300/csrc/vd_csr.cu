@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int* __
   if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_bsum_kernel(long long* bsum, int nb, DevStatus* st) {
+__global__ void __launch_bounds__(kScanThreads) scan_bsum_kernel(long long* bsum, int nb, long long* total,
+                                                                 DevStatus* st) {
   __shared__ long long wt[32];
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_bsum_kernel(long long* bsum
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    st->nnz = carry;
+    *total = carry;
     if (carry > 0x7fffffffLL) set_error(st, VD_ERR_TOO_LARGE);
   }
 }
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_bsum_kernel(long long* bsum
 __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int* __restrict__ counts, int n,
                                                                   const long long* __restrict__ bsum,
                                                                   int* __restrict__ offsets,
-                                                                  const DevStatus* st) {
+                                                                  const long long* __restrict__ total) {
   __shared__ long long wt[32];
   int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
   int c[kScanItems];
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_write_kernel(const int* __r
     if (base + k < n) offsets[base + k] = (int)run;
     run += c[k];
   }
-  if (base + kScanItems >= n && base < n) offsets[n] = (int)st->nnz;
+  if (base + kScanItems >= n && base < n) offsets[n] = (int)*total;
 }
 
 // one warp per row: copy the row's neighbours from its scratch row (or the
@@ -126,8 +127,8 @@ cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbor
   int nb = (n + kScanTile - 1) / kScanTile;
   if (recount) {
     scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(c.counts, n, block_sums);
-    scan_bsum_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb, c.st);
-    scan_write_kernel<<<nb, kScanThreads, 0, s>>>(c.counts, n, block_sums, offsets, c.st);
+    scan_bsum_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb, &c.st->nnz, c.st);
+    scan_write_kernel<<<nb, kScanThreads, 0, s>>>(c.counts, n, block_sums, offsets, &c.st->nnz);
   }
   if (neighbors && cap > 0) {
     int blocks = (n + 7) / 8;
@@ -136,6 +137,26 @@ cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbor
                                           neighbors, neighbors ? cap : 0, c.st);
   }
   finish_status_kernel<<<1, 1, 0, s>>>(c.st, neighbors ? cap : 0x7fffffffffffffffLL, nnz_out, user_status);
+  return cudaGetLastError();
+}
+
+__global__ void mesh_finish_kernel(const DevStatus* st, int64_t* nverts_out, int32_t* user_status) {
+  if (nverts_out) *nverts_out = st->nverts;
+  if (user_status) *user_status = st->error;
+}
+
+cudaError_t launch_mesh_finish(const DevStatus* st, int64_t* nverts_out, int32_t* user_status, cudaStream_t s) {
+  mesh_finish_kernel<<<1, 1, 0, s>>>(st, nverts_out, user_status);
+  return cudaGetLastError();
+}
+
+// Exclusive scan of n counts into offsets[n+1]; the total goes to *total.
+cudaError_t launch_scan(const int* counts, int n, int32_t* offsets, long long* block_sums, long long* total,
+                        DevStatus* st, cudaStream_t s) {
+  int nb = (n + kScanTile - 1) / kScanTile;
+  scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(counts, n, block_sums);
+  scan_bsum_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb, total, st);
+  scan_write_kernel<<<nb, kScanThreads, 0, s>>>(counts, n, block_sums, offsets, total);
   return cudaGetLastError();
 }
 

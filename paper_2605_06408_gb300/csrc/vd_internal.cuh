@@ -48,6 +48,7 @@ struct DevStatus {
   long long vertex_tests;
   long long new_vertices;
   long long pool_used;  // ints of the large-cell neighbour pool in use
+  long long nverts;     // vertices of the last mesh output
   long long refined_vertices;
   long long refined_volumes;
   long long ovf_reason[4];  // queue, vertices, planes, neighbours
@@ -280,6 +281,14 @@ struct BackBuffers {
   int list_cap;
   int* work;            // [2]
   const char* tape;     // the forward's tape, or nullptr (re-clip every cell)
+  // mesh output and vertex gradients
+  int mode;              // 0: gradients; 1: vertex count per cell; 2: vertex output
+  int* vcount;           // [n] by original index (mode 1)
+  const int32_t* voff;   // [n+1] vertex offsets (mode 2; mode 0 with gvert)
+  float* vout;           // [3 vcap] world positions (mode 2)
+  int32_t* vsites;       // [3 vcap] the other three defining sites (mode 2)
+  long long vcap;        // (mode 2)
+  const float* gvert;    // [3 V] gradient per vertex in mesh order, or nullptr
 };
 
 cudaError_t launch_weight_range(const float* w, int n, const SetInfo* sets, int nsets, unsigned* wr,
@@ -298,6 +307,9 @@ cudaError_t launch_cells_thread(const CellBuffers& c, int num_sms, cudaStream_t 
 cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbors, int64_t cap, int64_t* nnz_out,
                        long long* block_sums, int32_t* user_status, bool recount, cudaStream_t s);
 cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s);
+cudaError_t launch_scan(const int* counts, int n, int32_t* offsets, long long* block_sums, long long* total,
+                        DevStatus* st, cudaStream_t s);
+cudaError_t launch_mesh_finish(const DevStatus* st, int64_t* nverts_out, int32_t* user_status, cudaStream_t s);
 cudaError_t launch_inverse_perm(const int* perm, int n, int* inv, cudaStream_t s);
 cudaError_t launch_mark_losers(const uint64_t* keys, const float4* sites, const int* perm, int n,
                                unsigned char* loser, cudaStream_t s);

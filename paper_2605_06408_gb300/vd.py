@@ -28,7 +28,8 @@ VD_ERR_TIMEOUT = -7
 ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
     "vd_build", "vd_copy_neighbors", "vd_build_batched", "vd_backward", "vd_get_timings", "vd_get_status",
-    "vd_error_string", "vd_cells_noalloc", "vd_autotune", "vd_autotune_batched",
+    "vd_error_string", "vd_cells_noalloc", "vd_autotune", "vd_autotune_batched", "vd_cells_mesh",
+    "vd_backward_mesh",
 )
 VD_TUNE_FORCE = 1
 
@@ -45,6 +46,17 @@ class VdOut(ctypes.Structure):
         ("nnz_out", ctypes.c_void_p),
         ("volume", ctypes.c_void_p),
         ("centroid", ctypes.c_void_p),
+        ("status", ctypes.c_void_p),
+    ]
+
+
+class VdMesh(ctypes.Structure):
+    _fields_ = [
+        ("vertex_offsets", ctypes.c_void_p),
+        ("vertices", ctypes.c_void_p),
+        ("vertex_sites", ctypes.c_void_p),
+        ("capacity", ctypes.c_int64),
+        ("nverts_out", ctypes.c_void_p),
         ("status", ctypes.c_void_p),
     ]
 
@@ -118,6 +130,8 @@ def load_library(build_if_missing: bool = True):
         lib.vd_get_timings.argtypes = [P, ctypes.POINTER(VdTimings)]
         lib.vd_cells_noalloc.argtypes = [P, P, I64, VdBox, P, P, P, P, P, P]
         lib.vd_autotune.argtypes = [P, P, P, I64, VdBox, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(VdConfig), P]
+        lib.vd_cells_mesh.argtypes = [P, ctypes.POINTER(VdMesh), P]
+        lib.vd_backward_mesh.argtypes = [P, P, P, P, P, P, P, P]
         lib.vd_autotune_batched.argtypes = [P, P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(VdConfig), P]
         lib.vd_error_string.argtypes = [I]
@@ -348,8 +362,37 @@ class Context:
         return self._finish(out, s, n, sync)
 
     # ------------------------------------------------------------ backward
+    def mesh(self, capacity: Optional[int] = None):
+        """The vertices of every cell of the last build (vd_cells_mesh):
+        (vertex_offsets int32 [n+1], vertices float32 [V,3] world positions,
+        vertex_sites int32 [V,3] the other defining sites or -1-f for box
+        faces). The order is the one backward(grad_vertices=...) expects."""
+        n = self._last_n
+        dev = self.device
+        off = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        nv = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        cap = int(capacity) if capacity is not None else 64 * n
+
+        def run(cap):
+            verts = torch.empty(max(cap, 1), 3, dtype=torch.float32, device=dev)
+            sites = torch.empty(max(cap, 1), 3, dtype=torch.int32, device=dev)
+            m = VdMesh(off.data_ptr(), verts.data_ptr(), sites.data_ptr(), cap, nv.data_ptr(), st.data_ptr())
+            _check(self._lib.vd_cells_mesh(self._h, ctypes.byref(m), _stream_ptr(dev)), "vd_cells_mesh")
+            torch.cuda.synchronize(dev)
+            return verts, sites
+
+        verts, sites = run(cap)
+        total = int(nv.item())
+        if int(st.item()) == VD_ERR_CAPACITY or total > cap:
+            verts, sites = run(total)
+        elif int(st.item()) != VD_OK:
+            raise VdError(int(st.item()), "vd_cells_mesh")
+        return off, verts[:total], sites[:total]
+
     def backward(self, grad_volume: Optional[torch.Tensor], grad_centroid: Optional[torch.Tensor],
-                 want_weights: bool = True, recompute: bool = False):
+                 want_weights: bool = True, recompute: bool = False,
+                 grad_vertices: Optional[torch.Tensor] = None, vertex_offsets: Optional[torch.Tensor] = None):
         """Gradients (float32 [n,3], float32 [n] or None) of
         sum gv_i V_i + gc_i . g_i for the last build of this context."""
         n = self._last_n
@@ -357,6 +400,14 @@ class Context:
         gw = torch.empty(n, dtype=torch.float32, device=self.device) if want_weights else None
         gv = None if grad_volume is None else grad_volume.contiguous().float()
         gc = None if grad_centroid is None else grad_centroid.contiguous().float()
+        if grad_vertices is not None:
+            if recompute or vertex_offsets is None:
+                raise ValueError("vertex gradients need the mesh's vertex_offsets and recompute=False")
+            gvx = grad_vertices.contiguous().float()
+            rc = self._lib.vd_backward_mesh(self._h, _ptr(gv), _ptr(gc), _ptr(gvx), _ptr(vertex_offsets.contiguous()),
+                                            _ptr(gp), _ptr(gw), _stream_ptr(self.device))
+            _check(rc, "vd_backward_mesh")
+            return gp, gw
         rc = self._lib.vd_backward(self._h, _ptr(gv), _ptr(gc), _ptr(gp), _ptr(gw), 1 if recompute else 0,
                                    _stream_ptr(self.device))
         _check(rc, "vd_backward")
@@ -403,3 +454,35 @@ def cells(sites: torch.Tensor, weights: Optional[torch.Tensor] = None, bbox=((0,
         grad = sites.requires_grad or (weights is not None and weights.requires_grad)
         context = Context(sites.device.index or 0, {"tape": 1} if grad else None)
     return _CellsFn.apply(sites, weights, context, bbox)
+
+
+class _MeshCellsFn(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, sites, weights, context, bbox):
+        res = context.build(sites.detach(), None if weights is None else weights.detach(), bbox)
+        voff, verts, vsites = context.mesh()
+        fctx.context = context
+        fctx.build_id = context._builds
+        fctx.has_w = weights is not None
+        fctx.voff = voff
+        fctx.mark_non_differentiable(res.offsets, res.neighbors, voff, vsites)
+        return res.volume, res.centroid, verts, res.offsets, res.neighbors, voff, vsites
+
+    @staticmethod
+    def backward(fctx, gvol, gcen, gverts, _go, _gn, _gvo, _gvs):
+        if fctx.context._builds != fctx.build_id:
+            raise RuntimeError("the context was rebuilt after this forward; backward needs its own context")
+        gp, gw = fctx.context.backward(gvol, gcen, want_weights=fctx.has_w, grad_vertices=gverts,
+                                       vertex_offsets=fctx.voff)
+        return gp, (gw if fctx.has_w else None), None, None
+
+
+def mesh_cells(sites: torch.Tensor, weights: Optional[torch.Tensor] = None, bbox=((0, 0, 0), (1, 1, 1)),
+               context: Optional[Context] = None):
+    """Differentiable build with the explicit mesh: returns (volume,
+    centroid, vertices [V,3], offsets, neighbors, vertex_offsets,
+    vertex_sites). Gradients flow from volume, centroid and the vertex
+    positions to sites and weights, the cell combinatorics held fixed."""
+    if context is None:
+        context = Context(sites.device.index or 0, {"tape": 1})
+    return _MeshCellsFn.apply(sites, weights, context, bbox)

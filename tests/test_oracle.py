@@ -327,3 +327,57 @@ def test_fd_grad_matches_analytic_and_full_rebuild(weighted):
                 continue
             fd = (Lp - Lm) / (float(xp[k, a]) - float(xm[k, a]))
             assert fd == pytest.approx(gp_fd[k, a], rel=2e-5, abs=2e-6)
+
+
+def _vertex_key_grad(i, t):
+    # a fixed pseudo-random gradient per (cell, defining sites)
+    a, b, c = sorted(t)
+    return np.array([np.sin(0.37 * i + 0.11 * a + 0.05 * b + 0.02 * c),
+                     np.cos(0.29 * i - 0.07 * a + 0.13 * b - 0.03 * c),
+                     np.sin(0.19 * i + 0.17 * a - 0.09 * b + 0.23 * c)])
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_vertex_grad_matches_central_differences(weighted):
+    """oracle.vertex_grad (implicit differentiation of each vertex's 3x3
+    system) against differences of the vertices rebuilt around a perturbed
+    site, vertices matched by their defining sites."""
+    n = 60
+    x = W.uniform(n, 81)
+    w = W.power_weights(x, 82, scale=0.5) if weighted else None
+    cells = np.arange(n)
+    gp, gw = oracle.vertex_grad(x, w, BOX, cells, _vertex_key_grad)
+
+    def loss(xx, ww):
+        L, keys = 0.0, []
+        for i in cells:
+            pos, tri = oracle.cell_vertices(xx, ww, BOX, int(i))
+            for v, t in zip(pos, tri):
+                L += float(_vertex_key_grad(int(i), tuple(t)) @ (xx[i].astype(np.float64) + v))
+                keys.append((int(i),) + tuple(sorted(t)))
+        return L, sorted(keys)
+
+    checked = 0
+    for k in (5, 17, 33):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[k, a] = np.float32(x[k, a] + 2.0 ** -14)
+            xm[k, a] = np.float32(x[k, a] - 2.0 ** -14)
+            Lp, kp = loss(xp, w)
+            Lm, km = loss(xm, w)
+            if kp != km:
+                continue  # combinatorics changed within +-h
+            fd = (Lp - Lm) / (float(xp[k, a]) - float(xm[k, a]))
+            assert fd == pytest.approx(gp[k, a], rel=1e-4, abs=1e-5)
+            checked += 1
+        if weighted:
+            wp, wm = w.copy(), w.copy()
+            hw = max(2.0 ** -26, 64 * float(np.spacing(w[k])))
+            wp[k] = np.float32(w[k] + hw)
+            wm[k] = np.float32(w[k] - hw)
+            Lp, kp = loss(x, wp)
+            Lm, km = loss(x, wm)
+            if kp == km:
+                fd = (Lp - Lm) / (float(wp[k]) - float(wm[k]))
+                assert fd == pytest.approx(gw[k], rel=1e-4, abs=1e-4)
+    assert checked >= 6
