@@ -54,7 +54,11 @@ extern "C" {
 #define VD_ERR_NO_FORWARD (-5)    /* vd_backward without a matching forward build     */
 #define VD_ERR_TOO_LARGE (-6)     /* more sites than the index encoding supports      */
 #define VD_ERR_TIMEOUT (-7)       /* a bounded wait between warps of a block ran out   */
-                                  /*   (device side; outputs of that build not valid)  */
+                                  /*   (device side; outputs of that build not valid). */
+                                  /*   Test hook: with the environment variable        */
+                                  /*   VD_TEST_STALL_HELPER set when vd_create runs,   */
+                                  /*   every build of that context withholds one count */
+                                  /*   of the large-cell helping, so the wait runs out */
 
 /* ------------------------------------------------------------------ types */
 typedef struct vd_ctx vd_ctx;

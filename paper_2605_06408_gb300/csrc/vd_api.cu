@@ -4,6 +4,7 @@
 // the caller's stream; nothing here synchronises the host except
 // workspace growth (cudaMalloc) and vd_get_status.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -93,6 +94,9 @@ struct vd_ctx {
   bool ev_valid = false;
   bool ev_backward = false;
   int launches = 0;
+  // test hook (environment VD_TEST_STALL_HELPER at vd_create): one helping
+  // group of each build's large-cell pass is never counted
+  bool test_stall = false;
   // tape of the forward's cells for the adjoint (separate allocation)
   char* tape = nullptr;
   int64_t tape_cap = 0;
@@ -280,6 +284,7 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   c.st = ctx->st;
   c.cfg = ctx->cfg;
   c.tape = (ctx->cfg.tape && ctx->cfg.cell_mode == 0 && ctx->tape_cap >= ctx->last_n) ? ctx->tape : nullptr;
+  c.stall = ctx->test_stall ? ctx->work + 6 : nullptr;
   return c;
 }
 
@@ -312,6 +317,7 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   if (e != cudaSuccess) return VD_ERR_CUDA;
   cudaMemsetAsync(ctx->st, 0, sizeof(DevStatus), s);
   cudaMemsetAsync(ctx->work, 0, sizeof(int) * 8, s);
+  if (ctx->test_stall) cudaMemsetAsync(ctx->work + 6, 1, sizeof(int), s);  // arm the test hook's token
   cudaMemsetAsync(ctx->ovf_slot, 0xff, sizeof(int) * (size_t)n, s);
   cudaMemsetAsync(ctx->counts, 0, sizeof(int) * (size_t)n, s);
   // 1. keys: (set, weight stratum, Morton code in the set's box); input validation
@@ -421,6 +427,7 @@ int vd_create(vd_ctx** out, int device, const vd_config* cfg) {
   if (!ctx) return VD_ERR_CUDA;
   ctx->device = device;
   ctx->cfg = c;
+  ctx->test_stall = std::getenv("VD_TEST_STALL_HELPER") != nullptr;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
     delete ctx;
     return VD_ERR_CUDA;

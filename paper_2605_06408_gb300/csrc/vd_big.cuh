@@ -72,6 +72,7 @@ struct BigArena {
   uint32_t* cdirty;  // [kBigC / 32] chunks whose box is stale
   struct HelpBoard* hb;  // the block's helping board (forward large-cell kernel only)
   int* err;              // device error word
+  int* stall;            // test hook (see help_drain), or nullptr
 };
 
 constexpr int kDirBins = 6 * 64;
@@ -139,6 +140,7 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   A.cdirty = (uint32_t*)(w + 32 * 16 + 3 * 32 * 4 + kDirBins * 4);
   A.hb = nullptr;
   A.err = nullptr;
+  A.stall = nullptr;
   return A;
 }
 
@@ -536,8 +538,10 @@ __device__ inline int help_claim(HelpReq& r, int gen, int nch) {
 }
 
 // Work on request r through its groups; returns the number of groups done
-// once none is left to claim.
-__device__ inline int help_drain(HelpReq& r, int gen, long long& tested) {
+// once none is left to claim. Test hook: while the token `stall` is armed,
+// the first group claimed is never counted, so its owner's bounded wait runs
+// out and reports VD_ERR_TIMEOUT (nothing else waits on that count).
+__device__ inline int help_drain(HelpReq& r, int gen, long long& tested, int* stall) {
   const unsigned lane = lane_id();
   int groups = 0;
   while (true) {
@@ -558,7 +562,8 @@ __device__ inline int help_drain(HelpReq& r, int gen, long long& tested) {
     if (lane == 0) {
       if (cm) atomicOr(&r.cuts, cm);
       __threadfence_block();
-      atomicAdd(&r.done, q1 - q0);
+      const bool skip = stall != nullptr && atomicExch(stall, 0) != 0;
+      if (!skip) atomicAdd(&r.done, q1 - q0);
     }
     __syncwarp();
   }
@@ -599,7 +604,7 @@ __device__ inline uint32_t big_filter(const BigCell& c, const BigArena& A, int k
       atomicAdd(&r.seq, 1);
     }
     gen = __shfl_sync(FULL, gen, 0);
-    help_drain(r, gen, tested);
+    help_drain(r, gen, tested, A.stall);
     if (lane == 0) {
       long long it = 0;
       while (vload(&r.done) < nch) {
@@ -636,7 +641,7 @@ __device__ inline void big_help(const BigArena& A, long long& tested) {
       int s = vload(&r.seq);
       s = __shfl_sync(FULL, s, 0);
       if (!(s & 1)) continue;
-      if (help_drain(r, ((s >> 1) + 1) & 0x7ff, tested) > 0) worked = true;
+      if (help_drain(r, ((s >> 1) + 1) & 0x7ff, tested, A.stall) > 0) worked = true;
     }
     if (worked) continue;
     int live = vload(&A.hb->live);

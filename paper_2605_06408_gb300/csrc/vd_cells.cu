@@ -929,6 +929,7 @@ __global__ void big_cells_kernel(CellBuffers P) {
   extern __shared__ __align__(16) char big_smem[];
   A.hb = reinterpret_cast<HelpBoard*>(big_smem + kBigSmemPerWarp * kBigWarpsPerBlock);
   A.err = &P.st->error;
+  A.stall = P.stall;
   if (threadIdx.x < kBigWarpsPerBlock) {
     A.hb->req[threadIdx.x].seq = 0;
     A.hb->req[threadIdx.x].next = 0;

@@ -263,6 +263,7 @@ struct CellBuffers {
   int* work;             // [2] work counters (main pass, overflow pass)
   DevStatus* st;
   char* tape;            // [n * kTapeStride] or nullptr (no tape this build)
+  int* stall;            // test hook: armed token (one helping group is never counted), or nullptr
   vd_config cfg;
 };
 

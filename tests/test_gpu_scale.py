@@ -138,3 +138,30 @@ def test_surfaces_20M_forward_and_backward(vdmod):
     g = gp.cpu().numpy()[K].astype(np.float64)
     err = np.abs(g - fd).max(1) / np.maximum(np.abs(fd).max(1), 1e-30)
     assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
+
+
+def test_bounded_helping_wait_reports_timeout(vdmod, monkeypatch):
+    """Failure detection without a fault: with the test hook, one helping
+    group of the large-cell pass is never counted; its owner's bounded wait
+    runs out, the build reports VD_ERR_TIMEOUT instead of hanging, and the
+    device stays usable (a fresh context then builds correctly)."""
+    import time
+
+    x = W.mixture(1_000_000, 1)
+    w = W.power_weights(x, 2)
+    xs, ws = dev(x), dev(w)
+    monkeypatch.setenv("VD_TEST_STALL_HELPER", "1")
+    stalled = vdmod.Context(0)  # the hook is read when the context is created
+    monkeypatch.delenv("VD_TEST_STALL_HELPER")
+    t0 = time.perf_counter()
+    with pytest.raises(vdmod.VdError) as err:
+        stalled.build(xs, ws, W.UNIT_BOX)
+    assert err.value.code == vdmod.VD_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    ok = vdmod.Context(0)
+    res = ok.build(xs, ws, W.UNIT_BOX)
+    assert ok.status()["error"] == 0
+    samp = np.sort(W.rng_for(21).choice(len(x), 300, replace=False))
+    ref = oracle.cells(x, w, W.UNIT_BOX, cells=samp)
+    check_rows(res.offsets.cpu().numpy().astype(np.int64), res.neighbors.cpu().numpy(),
+               res.volume.cpu().numpy(), res.centroid.cpu().numpy(), ref, samp)
