@@ -91,6 +91,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(v, dist, device):
+    """The maximum of v over all ranks (None and single-process: v)."""
+    if dist is None or v is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank: int, world_size: int, ms: float) -> float:
+    """Whole-job Mcells/s: every rank builds its own set of cells_per_rank
+    sites (replicas, weak scaling), timed by the slowest rank."""
+    return cells_per_rank * world_size / (ms * 1e-3) / 1e6
+
+
 def make_workload(name: str, rank: int):
     """(xyz, weights or None, box, batch) where batch = (set offsets, boxes,
     weighted flags) for batched workloads, else None."""
@@ -516,17 +533,9 @@ def run_ours(args):
     h2d = 12 * n + (4 * n if w is not None else 0)
     d2h = 4 * (n + 1) + 4 * nnz + 16 * n
 
-    def reduce_max(v):
-        if dist is None or v is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = reduce_max(ms)
-    fb_ms = reduce_max(fb_ms)
-    e2e_ms = reduce_max(e2e_ms)
-    total_cells = n * ws
+    ms = max_over_ranks(ms, dist, dev)
+    fb_ms = max_over_ranks(fb_ms, dist, dev)
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -557,7 +566,7 @@ def run_ours(args):
 
     out = {
         "metric": METRIC,
-        "value": total_cells / (ms * 1e-3) / 1e6,
+        "value": job_rate(n, ws, ms),
         "unit": "Mcells/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -575,10 +584,10 @@ def run_ours(args):
                    "libvd": {k: v for k, v in ctx.config.items()},
                    "autotuned": not args.no_autotune, "autotune_s": tune_s,
                    "weight_ratio": args.weight_ratio if args.workload == "uniform1M_wratio" else None},
-        "fwd_bwd_mcells_s": None if fb_ms is None else total_cells / (fb_ms * 1e-3) / 1e6,
+        "fwd_bwd_mcells_s": None if fb_ms is None else job_rate(n, ws, fb_ms),
         "fwd_bwd_config": "the timed configuration with tape = 1 (the forward keeps its cells for the adjoint)",
         "fwd_bwd_ms_per_step": fb_ms,
-        "e2e": {"value": total_cells / (e2e_ms * 1e-3) / 1e6, "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(n, ws, e2e_ms), "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,
