@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_error_strings_and_null_arguments(lib):
     from paper_2605_06408_gb300 import vd
 
-    for code in range(0, -7, -1):
+    for code in range(0, -8, -1):
         assert len(lib.vd_error_string(code)) > 0
     assert lib.vd_build(None, None, None, 10, vd.VdBox(), None, None) == vd.VD_ERR_INVALID_ARG
     assert lib.vd_backward(None, None, None, None, None, 1, None) == vd.VD_ERR_INVALID_ARG
@@ -57,3 +57,46 @@ def test_workspace_bytes_grows_with_n(lib):
     assert 0 < a < b
     # ~0.5 KB per site: 20M sites fit easily in the GPU's memory
     assert lib.vd_workspace_bytes(20_000_000, 0) < 16 * 2**30
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "vd.h"
+int main(void) {
+  vd_config c;
+  if (vd_default_config(&c) != VD_OK) return 1;
+  if (c.leaf_size != 16 || c.verts_per_lane != 2 || c.tape != 0 || c.precision != 0) return 2;
+  if (vd_default_config(NULL) != VD_ERR_INVALID_ARG) return 3;
+  vd_box b = {{0.f, 0.f, 0.f}, {1.f, 1.f, 1.f}};
+  if (vd_build(NULL, NULL, NULL, 10, b, NULL, NULL) != VD_ERR_INVALID_ARG) return 4;
+  if (vd_cells_mesh(NULL, NULL, NULL) != VD_ERR_INVALID_ARG) return 5;
+  if (strlen(vd_error_string(VD_ERR_TIMEOUT)) == 0) return 6;
+  printf("%zu\n", vd_workspace_bytes(1000, 0));
+  return 0;
+}
+"""
+
+
+def test_plain_c_program_uses_the_library(lib, tmp_path):
+    """A C99 program compiles against include/vd.h, links libvd.so and
+    calls the host-side entry points (no GPU needed for these)."""
+    import shutil
+    import subprocess
+
+    from paper_2605_06408_gb300 import build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "prog.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "prog"
+    libdir = os.path.dirname(build.LIB)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lvd",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stderr)
+    assert int(run.stdout.strip()) > 0
