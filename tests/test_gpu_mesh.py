@@ -108,3 +108,33 @@ def test_mesh_autograd_function(vdmod):
     gp, gw = ctx.backward(gv, 2.0 * cen.detach(), grad_vertices=2.0 * verts2, vertex_offsets=voff2)
     assert torch.allclose(xs.grad, gp, rtol=1e-4, atol=1e-6 * gp.abs().max().item())
     assert torch.allclose(ws.grad, gw, rtol=1e-4, atol=1e-6 * gw.abs().max().item())
+
+
+def test_mesh_capacity_paths(vdmod):
+    """A too-small vertex buffer reports VD_ERR_CAPACITY with the size to
+    allocate (the wrapper retries); capacity 0 gives counts and offsets only."""
+    import ctypes
+
+    x, w = workload(False)
+    ctx = vdmod.Context(0)
+    ctx.build(dev(x), None, BOX)
+    off_full, verts_full, sites_full = ctx.mesh()
+    off_small, verts_small, sites_small = ctx.mesh(capacity=10)  # retried at the reported size
+    assert torch.equal(off_small, off_full) and torch.equal(sites_small, sites_full)
+    assert torch.equal(verts_small, verts_full)
+    n = len(x)
+    off = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    nv = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    m = vdmod.VdMesh(off.data_ptr(), None, None, 0, nv.data_ptr(), st.data_ptr())
+    lib = vdmod.load_library()
+    assert lib.vd_cells_mesh(ctx._h, ctypes.byref(m), None) == vdmod.VD_OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == vdmod.VD_OK and int(nv.item()) == len(verts_full)
+    assert torch.equal(off, off_full)
+    verts = torch.empty(5, 3, dtype=torch.float32, device="cuda")
+    sites = torch.empty(5, 3, dtype=torch.int32, device="cuda")
+    m = vdmod.VdMesh(off.data_ptr(), verts.data_ptr(), sites.data_ptr(), 5, nv.data_ptr(), st.data_ptr())
+    assert lib.vd_cells_mesh(ctx._h, ctypes.byref(m), None) == vdmod.VD_OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == vdmod.VD_ERR_CAPACITY and int(nv.item()) == len(verts_full)
