@@ -226,6 +226,20 @@ def cpu_oracle_rate(x, w, box, sample: int, seed: int = 7):
     return m / dt / 1e6, cores, dt, m
 
 
+def cpu_oracle_rate_1core(x, w, box, sample: int, seed: int = 8):
+    """The same oracle on one host thread (a smaller seeded sample).
+    Returns (Mcells/s, cells)."""
+    import oracle
+    from paper_2605_06408_gb300 import workloads as W
+
+    rng = W.rng_for(seed)
+    m = min(max(2000, sample // 50), len(x))
+    cells = np.sort(rng.choice(len(x), m, replace=False))
+    t0 = time.perf_counter()
+    oracle.cells(x, w, box, cells=cells, threads=1, max_nbrs=256)
+    return m / (time.perf_counter() - t0) / 1e6, m
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -561,8 +575,10 @@ def run_ours(args):
             cx = x[offs[s_big]:offs[s_big + 1]]
             cw = w[offs[s_big]:offs[s_big + 1]] if batch[2][s_big] else None
         rate, cores, dt, m = cpu_oracle_rate(cx, cw, box, args.cpu_sample)
+        rate1, m1 = cpu_oracle_rate_1core(cx, cw, box, args.cpu_sample)
         cpu = {"value": rate, "unit": "Mcells/s", "cores": cores, "kind": "oracle",
-               "sample": f"{m} seeded cells of {args.workload} ({dt:.1f} s, FP64 k-d tree oracle, all host cores)"}
+               "sample": f"{m} seeded cells of {args.workload} ({dt:.1f} s, FP64 k-d tree oracle, all host cores)",
+               "value_1core": rate1, "sample_1core": f"{m1} seeded cells, one host thread"}
 
     out = {
         "metric": METRIC,

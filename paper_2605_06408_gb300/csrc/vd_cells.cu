@@ -101,12 +101,60 @@ struct CellOut {
   bool fp64;
 };
 
+// The cell's record for the adjoint (tape): its vertices with plane indices
+// renumbered to the alive planes' order, and those planes' ids; a header of
+// -1 vertices when the cell does not fit a record. Out of line, like
+// cell_outputs: code that a build without a tape never runs stays out of
+// the once-per-cell path.
+template <int VPL, int PCAP, int QPL>
+static __device__ __noinline__ void write_tape(WarpSmem<VPL, PCAP, QPL>& S, char* rec, const int nv, uint32_t a0,
+                                               uint32_t a1, uint32_t a2, uint32_t a3) {
+  constexpr int NPW = PCAP / 32;
+  const unsigned lane = lane_id();
+  const uint32_t al[4] = {a0, a1, a2, a3};
+  uint32_t alive[NPW];
+  int pre[NPW], nf = 0;
+#pragma unroll
+  for (int w = 0; w < NPW; w++) {
+    alive[w] = al[w];
+    pre[w] = nf;
+    nf += __popc(alive[w]);
+  }
+  const bool fits = nv <= kTapeV && nf <= kTapeF;
+  if (fits) {
+    auto rank = [&](uint32_t f) -> uint32_t {
+      uint32_t r = 0;
+#pragma unroll
+      for (int w = 0; w < NPW; w++)
+        if ((f >> 5) == (uint32_t)w) r = (uint32_t)pre[w] + __popc(alive[w] & ((1u << (f & 31u)) - 1u));
+      return r;
+    };
+    float4* tv = reinterpret_cast<float4*>(rec + kTapeVOff);
+#pragma unroll 1
+    for (int t = (int)lane; t < nv; t += 32) {
+      const uint32_t T = S.nvt[t];
+      const uint32_t R = rank(T & 255u) | (rank((T >> 8) & 255u) << 8) | (rank((T >> 16) & 255u) << 16);
+      const float4 p = S.nvp[t];
+      tv[t] = make_float4(p.x, p.y, p.z, __uint_as_float(R));
+    }
+    int* tf = reinterpret_cast<int*>(rec + kTapeFOff);
+#pragma unroll
+    for (int w = 0; w < NPW; w++) {
+      const int f = 32 * w + (int)lane;
+      if ((alive[w] >> lane) & 1u) tf[rank((uint32_t)f)] = S.pid[f];
+    }
+  }
+  if (lane == 0) *reinterpret_cast<int4*>(rec) = make_int4(fits ? nv : -1, nf, 0, 0);
+}
+
 // The outputs of a finished cell from its vertices gathered in S (slot
 // order, nv of them, coordinate sums sx, sy, sz, alive planes a0..a3): the
 // neighbour row, the tape record, volume and centroid. Out of line: it runs
 // once per cell, and keeping it out of the traversal loop's code helps the
-// instruction cache. Returns false, writing nothing, if the neighbour list
-// is longer than a row.
+// instruction cache. For the same reason its loops stay rolled and its cold
+// branches (the tape, the FP64 volume) are calls: every kilobyte of code
+// here measurably slows the whole kernel. Returns false, writing nothing, if
+// the neighbour list is longer than a row.
 template <int VPL, int PCAP, int QPL>
 static __device__ __noinline__ bool cell_outputs(WarpSmem<VPL, PCAP, QPL>& S, const CellOut O, const int nv,
                                                  const float sx, const float sy, const float sz, uint32_t a0,
@@ -132,52 +180,21 @@ static __device__ __noinline__ bool cell_outputs(WarpSmem<VPL, PCAP, QPL>& S, co
   }
   __syncwarp();
   if (nvals > O.stride) return false;  // more neighbours than a fast-path row holds
+#pragma unroll 1
   for (int t = (int)lane; t < nvals; t += 32) {
     int v = (int)S.otri[t];
     int rank = 0;
+#pragma unroll 1
     for (int u = 0; u < nvals; u++) rank += (int)S.otri[u] < v;
     row[rank] = v;
   }
-  if (O.tape) {
-    // the cell for the adjoint: vertices with plane indices renumbered to
-    // the alive planes' order, and those planes' ids
-    char* rec = O.tape + (size_t)si * kTapeStride;
-    int pre[NPW], nf = 0;
-#pragma unroll
-    for (int w = 0; w < NPW; w++) {
-      pre[w] = nf;
-      nf += __popc(alive[w]);
-    }
-    const bool fits = nv <= kTapeV && nf <= kTapeF;
-    if (fits) {
-      auto rank = [&](uint32_t f) -> uint32_t {
-        uint32_t r = 0;
-#pragma unroll
-        for (int w = 0; w < NPW; w++)
-          if ((f >> 5) == (uint32_t)w) r = (uint32_t)pre[w] + __popc(alive[w] & ((1u << (f & 31u)) - 1u));
-        return r;
-      };
-      float4* tv = reinterpret_cast<float4*>(rec + kTapeVOff);
-      for (int t = (int)lane; t < nv; t += 32) {
-        const uint32_t T = S.nvt[t];
-        const uint32_t R = rank(T & 255u) | (rank((T >> 8) & 255u) << 8) | (rank((T >> 16) & 255u) << 16);
-        const float4 p = S.nvp[t];
-        tv[t] = make_float4(p.x, p.y, p.z, __uint_as_float(R));
-      }
-      int* tf = reinterpret_cast<int*>(rec + kTapeFOff);
-#pragma unroll
-      for (int w = 0; w < NPW; w++) {
-        const int f = 32 * w + (int)lane;
-        if ((alive[w] >> lane) & 1u) tf[rank((uint32_t)f)] = S.pid[f];
-      }
-    }
-    if (lane == 0) *reinterpret_cast<int4*>(rec) = make_int4(fits ? nv : -1, nf, 0, 0);
-  }
+  if (O.tape) write_tape<VPL, PCAP, QPL>(S, O.tape + (size_t)si * kTapeStride, nv, a0, a1, a2, a3);
   // volume and first moment: tetrahedra (c, g_f, v, w) for every directed
   // edge v -> w of face f (w = the other end of the edge), g_f = the foot of
   // c on plane f; c = vertex mean
   float cx = sx / nv, cy = sy / nv, cz = sz / nv;
   float V = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, Sabs = 0.f, emax = 0.f;
+#pragma unroll 1
   for (int it = (int)lane; it < 3 * nv; it += 32) {
     int t = it / 3, rho = it % 3;
     uint32_t T = S.nvt[t];
@@ -217,9 +234,10 @@ static __device__ __noinline__ bool cell_outputs(WarpSmem<VPL, PCAP, QPL>& S, co
     double Mxd, Myd, Mzd;
     volume_fp64(S, nv, O.me, O.box, O.box + 3, O.sites, (double)cx, (double)cy, (double)cz, Vd, Mxd, Myd, Mzd);
     if (Vd > 0.0) {
-      ox += Mxd / Vd;
-      oy += Myd / Vd;
-      oz += Mzd / Vd;
+      const double iv = 1.0 / Vd;
+      ox += Mxd * iv;
+      oy += Myd * iv;
+      oz += Mzd * iv;
     }
     if (lane == 0) S.ct.refvol++;
   } else if (V > 0.0f) {
