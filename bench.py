@@ -271,11 +271,12 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU
 
-def fused_traffic_from_profiles(src_hash: str):
+def fused_traffic_from_profiles(src_hash: str, workload: str):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and for this
+    workload (the summary covers mixture1M only)."""
     path = os.path.join(ROOT, "profiles", "cells_kernel_mixture1M.md")
-    if not os.path.exists(path):
+    if workload != "mixture1M" or not os.path.exists(path):
         return None
     txt = open(path).read()
     h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
@@ -564,7 +565,7 @@ def run_ours(args):
     cms = statistics.mean(cells_ms)
     achieved = flop / (cms * 1e-3)
     src_hash = kernel_source_hash()
-    traffic = fused_traffic_from_profiles(src_hash)
+    traffic = fused_traffic_from_profiles(src_hash, args.workload)
 
     cpu = None
     if not args.no_cpu_baseline:
