@@ -110,11 +110,15 @@ typedef struct {
                            /*    faces) on a tape of 1 KB per site for              */
                            /*    vd_backward(recompute = 0), if the tape fits in    */
                            /*    half of the free device memory when the workspace  */
-                           /*    is sized; otherwise, and with 0 (default: no       */
-                           /*    backward planned), the adjoint re-clips every cell */
+                           /*    is sized, and the polytopes of larger cells on a   */
+                           /*    second pool (128 B per site, at least 64 MB) if    */
+                           /*    that fits in a quarter of what is left; cells with */
+                           /*    no record, and every cell with 0 (default: no      */
+                           /*    backward planned), are re-clipped by the adjoint   */
                            /*    (memory asks for recomputing). Set it when a       */
                            /*    backward follows: the tape costs ~3% of a forward  */
-                           /*    and saves ~half of the adjoint                     */
+                           /*    and saves half of the adjoint (nine tenths on      */
+                           /*    power diagrams with very large cells)              */
   int32_t precision;       /* 0: mixed (default): FP32 predicates, those within     */
                            /*    their error bound of zero re-evaluated in FP64,    */
                            /*    ill-conditioned vertices re-solved and suspect     */

@@ -3,6 +3,7 @@
 // fused per-cell kernel; then CSR compaction). Everything is enqueued on
 // the caller's stream; nothing here synchronises the host except
 // workspace growth (cudaMalloc) and vd_get_status.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -101,6 +102,9 @@ struct vd_ctx {
   char* tape = nullptr;
   int64_t tape_cap = 0;
   bool tape_valid = false;
+  // large-cell tape: polytopes of the cells past the register path
+  char* btape = nullptr;
+  int64_t btape_cap = 0;
   // autotuner: best configuration per (log2 n, weighted, set count)
   std::map<std::tuple<int, int, int>, vd_config> tuned;
 };
@@ -144,6 +148,9 @@ static int release(vd_ctx* ctx) {
   ctx->tape = nullptr;
   ctx->tape_cap = 0;
   ctx->tape_valid = false;
+  if (ctx->btape) cudaFree(ctx->btape);
+  ctx->btape = nullptr;
+  ctx->btape_cap = 0;
   ctx->bytes = 0;
   ctx->cap_n = 0;
   ctx->have_forward = false;
@@ -187,12 +194,19 @@ static Layout make_layout(int64_t n, int num_sms) {
 
 // The tape (1 KB per site) when the configuration asks for it and it fits in
 // half of the free device memory; otherwise none (the adjoint re-clips).
+// Beside it, the large-cell tape (kBigTapePerSite bytes per site, at least
+// 64 MB) if that fits in a quarter of what is left; cells whose polytope
+// does not fit there are re-clipped by the adjoint.
 static void reserve_tape(vd_ctx* ctx) {
   const bool want = ctx->cfg.tape != 0 && ctx->cfg.cell_mode == 0;
   if (!want || ctx->tape_cap >= ctx->cap_n) return;
   if (ctx->tape) cudaFree(ctx->tape);
   ctx->tape = nullptr;
   ctx->tape_cap = 0;
+  ctx->tape_valid = false;
+  if (ctx->btape) cudaFree(ctx->btape);
+  ctx->btape = nullptr;
+  ctx->btape_cap = 0;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return;
   const size_t bytes = (size_t)kTapeStride * (size_t)ctx->cap_n;
@@ -203,6 +217,15 @@ static void reserve_tape(vd_ctx* ctx) {
     return;
   }
   ctx->tape_cap = ctx->cap_n;
+  const size_t bbytes = std::max((size_t)64 << 20, (size_t)kBigTapePerSite * (size_t)ctx->cap_n);
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && bbytes <= free_b / 4) {
+    if (cudaMalloc(&ctx->btape, bbytes) == cudaSuccess) {
+      ctx->btape_cap = (int64_t)bbytes;
+    } else {
+      cudaGetLastError();
+      ctx->btape = nullptr;
+    }
+  }
 }
 
 static int reserve(vd_ctx* ctx, int64_t n) {
@@ -285,6 +308,8 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   c.cfg = ctx->cfg;
   c.tape = (ctx->cfg.tape && ctx->cfg.cell_mode == 0 && ctx->tape_cap >= ctx->last_n) ? ctx->tape : nullptr;
   c.stall = ctx->test_stall ? ctx->work + 6 : nullptr;
+  c.btape = c.tape ? ctx->btape : nullptr;
+  c.btape_cap = c.tape ? ctx->btape_cap : 0;
   return c;
 }
 

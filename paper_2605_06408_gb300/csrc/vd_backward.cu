@@ -173,6 +173,7 @@ __device__ bool back_cell(const BackBuffers& B, BackSmem<VPL, PCAP>& SM, int si)
     // recomputed from their ids exactly as the forward computed them)
     const char* rec = B.tape + (size_t)si * kTapeStride;
     const int4 h = *reinterpret_cast<const int4*>(rec);
+    if (h.x == -2) return false;  // a large cell with a record on the large-cell tape
     if (h.x > 0) {
       nv = h.x;
       const int nf = h.y;
@@ -395,6 +396,57 @@ __global__ void back_kernel(BackBuffers B) {
 
 // ---------------------------------------------------------------- large cells
 
+// Restore the forward's polytope of large cell si from the large-cell tape
+// (planes recomputed from their ids exactly as the forward computed them).
+// False, with the arena untouched, if the cell has no valid record.
+__device__ inline bool big_tape_read(BigCell& c, const BigArena& A, const BackBuffers& B, int si) {
+  const CellBuffers& P = B.c;
+  const int4 h = *reinterpret_cast<const int4*>(B.tape + (size_t)si * kTapeStride);
+  if (h.x != -2 || !P.btape) return false;
+  const long long off = (long long)(((unsigned long long)(unsigned)h.w << 32) | (unsigned long long)(unsigned)h.z);
+  if (off < 0 || (off & 15) || off + 16 > P.btape_cap) return false;
+  const char* rec = P.btape + off;
+  const int4 rh = *reinterpret_cast<const int4*>(rec);
+  const int nv = rh.x, npl = rh.y;
+  if (nv <= 0 || nv > kBigV || npl <= 0 || npl > kBigP || npl != h.y || off + big_tape_bytes(nv, npl) > P.btape_cap)
+    return false;
+  const float4* vp = reinterpret_cast<const float4*>(rec + 16);
+  const uint64_t* vt = reinterpret_cast<const uint64_t*>(rec + 16 + 16 * (size_t)nv);
+  const int* pid = reinterpret_cast<const int*>(rec + 16 + 24 * (size_t)nv);
+  const unsigned lane = lane_id();
+  bool ok = true;
+  for (int p = (int)lane; p < npl; p += 32) ok = ok && pid[p] >= -6 && pid[p] < P.n;
+  for (int i = (int)lane; i < nv; i += 32) {
+    const uint64_t T = vt[i];
+    ok = ok && (int)bfield(T, 0) < npl && (int)bfield(T, 1) < npl && (int)bfield(T, 2) < npl;
+  }
+  if (!__all_sync(FULL, ok)) return false;
+  for (int i = (int)lane; i < nv; i += 32) {
+    A.vp[i] = vp[i];
+    A.vt[i] = vt[i];
+  }
+  for (int p = (int)lane; p < npl; p += 32) {
+    const int id = pid[p];
+    PlaneT<float> H;
+    if (id >= 0) {
+      const float4 q = P.sites[id];
+      H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+    } else {
+      H = box_plane<float>(-1 - id, c.me.x, c.me.y, c.me.z, c.lo, c.hi);
+    }
+    A.pl[p] = make_float4(H.nx, H.ny, H.nz, H.b);
+    A.pe[p] = H.e;
+    A.pid[p] = id;
+  }
+  c.nv = nv;
+  c.nlive = nv;
+  c.nfree = 0;
+  c.unsorted = 0;
+  c.npl = npl;
+  __syncwarp();
+  return true;
+}
+
 __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, Counters& ct) {
   const CellBuffers& P = B.c;
   const unsigned lane = lane_id();
@@ -411,42 +463,46 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
   }
   const int cnt = P.counts[orig_i];
   if (cnt <= 0) return true;
-  big_init(c, A, 0);
-  const int slot = P.ovf_slot[orig_i];
-  const int* row = slot >= 0 ? P.pool + slot : P.scratch + (size_t)orig_i * P.stride;
-  for (int c0 = 0; c0 < cnt; c0 += 32) {
-    int t = c0 + (int)lane;
-    bool keep = t < cnt;
-    int j = 0;
-    PlaneT<float> H;
-    H.nx = H.ny = H.nz = H.b = H.e = 0.f;
-    float dkey = INFINITY;
-    if (keep) {
-      j = B.inv_perm[row[t] + SI.first];
-      float4 q = P.sites[j];
-      H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
-      dkey = H.b;
+  // the forward's polytope from the large-cell tape, else re-clipped from
+  // the cell's neighbour row
+  if (!(B.tape && big_tape_read(c, A, B, si))) {
+    big_init(c, A, 0);
+    const int slot = P.ovf_slot[orig_i];
+    const int* row = slot >= 0 ? P.pool + slot : P.scratch + (size_t)orig_i * P.stride;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      int t = c0 + (int)lane;
+      bool keep = t < cnt;
+      int j = 0;
+      PlaneT<float> H;
+      H.nx = H.ny = H.nz = H.b = H.e = 0.f;
+      float dkey = INFINITY;
+      if (keep) {
+        j = B.inv_perm[row[t] + SI.first];
+        float4 q = P.sites[j];
+        H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
+        dkey = H.b;
+      }
+      uint32_t km = __ballot_sync(FULL, keep);
+      while (km) {
+        uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
+        uint32_t mn = __reduce_min_sync(FULL, key);
+        int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
+        PlaneT<float> Hb;
+        Hb.nx = __shfl_sync(FULL, H.nx, src);
+        Hb.ny = __shfl_sync(FULL, H.ny, src);
+        Hb.nz = __shfl_sync(FULL, H.nz, src);
+        Hb.b = __shfl_sync(FULL, H.b, src);
+        Hb.e = __shfl_sync(FULL, H.e, src);
+        int hj = __shfl_sync(FULL, j, src);
+        if ((int)lane == src) keep = false;
+        km &= ~(1u << src);
+        int rc = big_clip(c, A, Hb, hj, P.sites, ct, false);
+        if (rc == CLIP_OVERFLOW) return false;
+        if (rc == CLIP_EMPTY) return true;
+      }
     }
-    uint32_t km = __ballot_sync(FULL, keep);
-    while (km) {
-      uint32_t key = keep ? f2o(dkey) : 0xffffffffu;
-      uint32_t mn = __reduce_min_sync(FULL, key);
-      int src = __ffs(__ballot_sync(FULL, keep && key == mn)) - 1;
-      PlaneT<float> Hb;
-      Hb.nx = __shfl_sync(FULL, H.nx, src);
-      Hb.ny = __shfl_sync(FULL, H.ny, src);
-      Hb.nz = __shfl_sync(FULL, H.nz, src);
-      Hb.b = __shfl_sync(FULL, H.b, src);
-      Hb.e = __shfl_sync(FULL, H.e, src);
-      int hj = __shfl_sync(FULL, j, src);
-      if ((int)lane == src) keep = false;
-      km &= ~(1u << src);
-      int rc = big_clip(c, A, Hb, hj, P.sites, ct, false);
-      if (rc == CLIP_OVERFLOW) return false;
-      if (rc == CLIP_EMPTY) return true;
-    }
+    big_compact(c, A);
   }
-  big_compact(c, A);
   if (B.mode == 1) {
     if (lane == 0) B.vcount[orig_i] = c.nv;
     return true;

@@ -144,6 +144,16 @@ __device__ inline BigArena big_arena(char* base, int slot) {
   return A;
 }
 
+// Large-cell tape record (the forward's polytope of a cell that left the
+// register path, so that the adjoint restores it instead of re-clipping):
+// int4 (nv, npl, 0, 0), nv float4 vertices, nv uint64 plane triplets, npl
+// plane ids; 16-byte aligned. The site's regular tape header then reads
+// (-2, npl, low and high 32 bits of the record's byte offset).
+constexpr long long kBigTapePerSite = 128;  // pool bytes reserved per site
+__host__ __device__ inline long long big_tape_bytes(int nv, int npl) {
+  return (16 + 24LL * nv + 4LL * npl + 15) & ~15LL;
+}
+
 struct BigCell {
   float4 me;
   float lo[3], hi[3];

@@ -725,6 +725,33 @@ __device__ inline void big_volume(const BigCell& c, const BigArena& A, const flo
 }
 
 // Returns false if the cell overflowed even the large capacity.
+// The finished (compacted) polytope of a large cell on the large-cell tape,
+// and the site's tape header pointing at it; a cell that does not fit keeps
+// the header -1 (the adjoint re-clips it).
+__device__ inline void big_tape_write(const BigCell& c, const BigArena& A, const CellBuffers& P, int si) {
+  const unsigned lane = lane_id();
+  const long long bytes = big_tape_bytes(c.nv, c.npl);
+  unsigned long long off = 0;
+  if (lane == 0) off = atomicAdd((unsigned long long*)&P.st->btape_used, (unsigned long long)bytes);
+  off = __shfl_sync(FULL, off, 0);
+  if ((long long)off + bytes > P.btape_cap) return;
+  char* rec = P.btape + off;
+  float4* vp = reinterpret_cast<float4*>(rec + 16);
+  uint64_t* vt = reinterpret_cast<uint64_t*>(rec + 16 + 16 * (size_t)c.nv);
+  int* pid = reinterpret_cast<int*>(rec + 16 + 24 * (size_t)c.nv);
+  for (int i = (int)lane; i < c.nv; i += 32) {
+    vp[i] = A.vp[i];
+    vt[i] = A.vt[i];
+  }
+  for (int p = (int)lane; p < c.npl; p += 32) pid[p] = A.pid[p];
+  if (lane == 0) {
+    *reinterpret_cast<int4*>(rec) = make_int4(c.nv, c.npl, 0, 0);
+    *reinterpret_cast<int4*>(P.tape + (size_t)si * kTapeStride) =
+        make_int4(-2, c.npl, (int)(unsigned)(off & 0xffffffffull), (int)(unsigned)(off >> 32));
+  }
+  __syncwarp();
+}
+
 __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, Counters& ct, long long& empties) {
   const unsigned lane = lane_id(), lt = lanemask_lt();
   const bool counters = P.cfg.counters != 0;
@@ -895,6 +922,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     cnt += __popc(mk);
   }
   __syncwarp();
+  if (P.btape && P.tape) big_tape_write(c, A, P, si);
   long long off = 0;
   if (cnt <= P.stride) {
     // short list: the cell's regular row

@@ -52,6 +52,7 @@ struct DevStatus {
   long long refined_vertices;
   long long refined_volumes;
   long long ovf_reason[4];  // queue, vertices, planes, neighbours
+  long long btape_used;     // bytes of the large-cell tape in use
 };
 
 __device__ inline void set_error(DevStatus* st, int code) { atomicCAS(&st->error, 0, code); }
@@ -265,6 +266,8 @@ struct CellBuffers {
   char* tape;            // [n * kTapeStride] or nullptr (no tape this build)
   int* stall;            // test hook: armed token (one helping group is never counted), or nullptr
   vd_config cfg;
+  char* btape;           // large-cell tape (polytopes of cells past the register path), or nullptr
+  long long btape_cap;   // its bytes
 };
 
 constexpr int kSortThreads = 512;
