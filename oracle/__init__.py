@@ -24,7 +24,8 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-STAT_NAMES = ("ambiguous", "degenerate", "orient_fail", "topo_fail", "clips", "tests", "empty", "facewalk_fail")
+STAT_NAMES = ("ambiguous", "degenerate", "orient_fail", "topo_fail", "clips", "tests", "empty", "facewalk_fail",
+              "exact_resolved")
 
 ERRORS = {
     -1: "invalid argument",
@@ -65,6 +66,14 @@ def _load():
             lib.oracle_cell_vertices.argtypes = [P, P, I64, P, P, I64, C, C, P, P, I32]
             lib.oracle_cell_vertices.restype = C
             lib.oracle_stat_count.restype = C
+            lib.oracle_exact_side.argtypes = [P, P, I64, P, P, I64, P]
+            lib.oracle_exact_side.restype = C
+            lib.oracle_session_open.argtypes = [P, P, I64, P, P, C, C, P]
+            lib.oracle_session_open.restype = P
+            lib.oracle_session_cells.argtypes = [P, P, I64, P, P, P, I64, P, P, P, P, P, C]
+            lib.oracle_session_cells.restype = C
+            lib.oracle_session_close.argtypes = [P]
+            lib.oracle_session_close.restype = None
             lib.oracle_fd_grad.argtypes = [P, P, I64, P, P, P, P, P, P, P, I64, P, P, P, P, C]
             lib.oracle_fd_grad.restype = C
             _lib = lib
@@ -127,18 +136,73 @@ def cells(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, mode="kd", exact
             continue
         _check(rc)
         break
+    return _cells_result(offsets, nb, counts, vol, cen, nv, nf, st)
+
+
+def _cells_result(offsets, nb, counts, vol, cen, nv, nf, st):
     indices = nb[: offsets[-1]].copy()
     return {
         "counts": counts,
         "offsets": offsets,
         "indices": indices,
-        "nbrs": np.split(indices, offsets[1:-1]) if m else [],
+        "nbrs": np.split(indices, offsets[1:-1]) if counts.shape[0] else [],
         "vol": vol,
         "cen": cen,
         "nverts": nv,
         "nfaces": nf,
         "stats": dict(zip(STAT_NAMES, st[:-1].tolist())),
     }
+
+
+class Session:
+    """One point set kept set up (duplicate marks, k-d tree) across calls:
+    ``Session(xyz, w, bbox).cells(cells)`` returns what ``cells(xyz, w,
+    bbox, cells=cells)`` returns, with the same arithmetic, without building
+    the tree again for every sample of cells."""
+
+    def __init__(self, xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), mode="kd", exact=False):
+        self._lib = _load()
+        self.xyz, self.w, self.lo, self.hi = _prep(xyz, w, bbox)
+        rc = ctypes.c_int(0)
+        self._h = self._lib.oracle_session_open(_ptr(self.xyz), _ptr(self.w), self.xyz.shape[0], _ptr(self.lo),
+                                                _ptr(self.hi), 0 if mode == "brute" else 1, 1 if exact else 0,
+                                                ctypes.byref(rc))
+        if not self._h:
+            _check(rc.value or -5)
+
+    def cells(self, cells=None, threads=None):
+        lib = self._lib
+        n = self.xyz.shape[0]
+        idx = None if cells is None else np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+        m = n if idx is None else idx.shape[0]
+        cap = 20 * m + 1024
+        while True:
+            counts = np.zeros(m, np.int32)
+            offsets = np.zeros(m + 1, np.int64)
+            nb = np.zeros(cap, np.int32)
+            vol = np.zeros(m, np.float64)
+            cen = np.zeros((m, 3), np.float64)
+            nv = np.zeros(m, np.int32)
+            nf = np.zeros(m, np.int32)
+            st = np.zeros(lib.oracle_stat_count() + 1, np.int64)
+            rc = lib.oracle_session_cells(self._h, _ptr(idx), m, _ptr(counts), _ptr(offsets), _ptr(nb), cap,
+                                          _ptr(vol), _ptr(cen), _ptr(nv), _ptr(nf), _ptr(st), _threads(threads))
+            if rc == -3 and st[-1] > cap:
+                cap = int(st[-1])
+                continue
+            _check(rc)
+            return _cells_result(offsets, nb, counts, vol, cen, nv, nf, st)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.oracle_session_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def grad(xyz, w, bbox, c, d, cells=None, threads=None):
@@ -184,6 +248,20 @@ def fd_grad(xyz, w, bbox, offsets, nbrs, c, d, sites, hx, hw=None, threads=None)
                             _ptr(idx), m, _ptr(hx), _ptr(hwa), _ptr(gp), _ptr(gw), _threads(threads))
     _check(rc)
     return gp, gw
+
+
+def exact_side(xyz, w, bbox, i, planes):
+    """Exact sign (+1 / -1 / 0) of n_h . v - b_h, where v is the vertex of
+    the planes of planes[0..2] in the frame of site i and h the plane of
+    planes[3] (site indices, or -1-f for box face f), from the oracle's
+    expansion arithmetic."""
+    lib = _load()
+    xyz, w, lo, hi = _prep(xyz, w, bbox)
+    ids = np.ascontiguousarray(np.asarray(planes, dtype=np.int64).reshape(4))
+    r = lib.oracle_exact_side(_ptr(xyz), _ptr(w), xyz.shape[0], _ptr(lo), _ptr(hi), int(i), _ptr(ids))
+    if r not in (-1, 0, 1):
+        raise RuntimeError(f"oracle_exact_side returned {r}")
+    return r
 
 
 def certify(xyz, w=None, bbox=((0, 0, 0), (1, 1, 1)), cells=None, exact=False, threads=None):

@@ -34,7 +34,12 @@
  *     T = n_h . (D1,D2,D3) - b_h * D0 > 0
  * (T = D0 * s_v and D0 > 0 by the orientation invariant). Two modes:
  *   - FP64: T in double with a Shewchuk-style static bound built from the
- *     permanents of the same minors; |T| below it counts as "ambiguous".
+ *     permanents of the same minors; when |T| is below that bound the sign
+ *     is taken exactly instead, in floating-point expansion arithmetic
+ *     (Shewchuk 1997: TwoSum, FMA TwoProduct, Grow-Expansion) from the
+ *     sites' coordinates and weights, as sign(T) * sign(D0). Every sign is
+ *     therefore exact; "exact_resolved" counts the predicates that needed
+ *     it, "degenerate" those whose exact value is 0 (outside means > 0).
  *   - exact: inputs on a 2^-20 coordinate / 2^-40 weight grid give integer
  *     plane rows, and T is computed exactly in __int128.
  *
@@ -70,15 +75,16 @@ typedef __int128 i128;
 
 /* statistics slots written to the caller's stats[] array */
 enum {
-  ST_AMBIGUOUS = 0,   /* FP64 predicates with |T| inside the error bound  */
-  ST_DEGENERATE = 1,  /* exact predicates with T == 0                     */
+  ST_AMBIGUOUS = 0,   /* predicates whose sign could not be certified     */
+  ST_DEGENERATE = 1,  /* exact predicates with T == 0 (or D0 == 0)        */
   ST_ORIENT_FAIL = 2, /* exact mode: a new vertex with D0 <= 0            */
   ST_TOPO_FAIL = 3,   /* hole walk could not reach every outside vertex   */
   ST_CLIPS = 4,       /* clips that removed at least one vertex           */
   ST_TESTS = 5,       /* candidate planes tested against the cell         */
   ST_EMPTY = 6,       /* empty cells                                      */
   ST_FACEWALK_FAIL = 7,
-  ST_N = 8
+  ST_EXACT = 8,       /* FP64 predicates inside the bound, signed exactly */
+  ST_N = 9
 };
 
 static const double EPS = 1.1102230246251565e-16; /* 2^-53 */
@@ -91,6 +97,7 @@ typedef struct {
   double b;      /* right-hand side                                    */
   double bmag;   /* magnitude bound used by the error bound of b       */
   int64_t site;  /* >= 0: site index; < 0: box face -1-k               */
+  int64_t owner; /* the cell's site i (the plane is in its frame)      */
   int64_t N[3];  /* exact mode: integer row                            */
   int64_t B;
 } plane_t;
@@ -210,6 +217,7 @@ static void make_site_plane(const problem_t* pr, int64_t i, int64_t j, plane_t* 
   P->b = 0.5 * (nn + (wi - wj));
   P->bmag = 0.5 * (nn + fabs(wi) + fabs(wj));
   P->site = j;
+  P->owner = i;
   if (pr->exact) {
     int64_t nn_i = 0;
     for (int k = 0; k < 3; k++) {
@@ -231,6 +239,7 @@ static void make_box_plane(const problem_t* pr, int64_t i, int k, plane_t* P) {
   P->b = (k & 1) ? (pi - pr->lo[ax]) : (pr->hi[ax] - pi);
   P->bmag = fabs(P->b);
   P->site = -1 - k;
+  P->owner = i;
   if (pr->exact) {
     P->N[0] = P->N[1] = P->N[2] = 0;
     P->N[ax] = (k & 1) ? -1 : 1;
@@ -316,9 +325,176 @@ static void vertex_from_planes(const cell_t* C, int exact, int a, int b, int c, 
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* exact signs by floating-point expansions (Shewchuk, "Adaptive precision
+ * floating-point arithmetic and fast robust geometric predicates", 1997).
+ * An expansion is an array of doubles whose exact sum is the value; built
+ * only by Grow-Expansion with zero elimination, it is nonoverlapping and
+ * ordered by increasing magnitude (Shewchuk's Theorem 10, round-to-nearest),
+ * so its sign is the sign of its last component. Inputs here are float32
+ * coordinates and weights (or FP64 for a finite-difference override), far
+ * from overflow and underflow, so TwoSum and TwoProduct are exact.        */
+
+typedef struct {
+  double* c;
+  int n, cap;
+  int overflow;
+} xp_t;
+
+#define XP_CAP 2048
+
+/* a + b = *s + *e exactly (Knuth's TwoSum) */
+static void two_sum(double a, double b, double* s, double* e) {
+  double x = a + b;
+  double bv = x - a;
+  double av = x - bv;
+  *s = x;
+  *e = (a - av) + (b - bv);
+}
+
+/* a * b = *p + *e exactly (TwoProduct with a fused multiply-add) */
+static void two_prod(double a, double b, double* p, double* e) {
+  double x = a * b;
+  *p = x;
+  *e = fma(a, b, -x);
+}
+
+static void xp_init(xp_t* X, double* buf) {
+  X->c = buf;
+  X->n = 0;
+  X->cap = XP_CAP;
+  X->overflow = 0;
+}
+
+/* X += b (Grow-Expansion, zero components dropped) */
+static void xp_grow(xp_t* X, double b) {
+  if (b == 0.0) return;
+  double q = b;
+  int m = 0;
+  for (int k = 0; k < X->n; k++) {
+    double s, e;
+    two_sum(q, X->c[k], &s, &e);
+    q = s;
+    if (e != 0.0) X->c[m++] = e;
+  }
+  if (q != 0.0) {
+    if (m >= X->cap) {
+      X->overflow = 1;
+      return;
+    }
+    X->c[m++] = q;
+  }
+  X->n = m;
+}
+
+static int xp_sign(const xp_t* X) {
+  if (X->n == 0) return 0;
+  return X->c[X->n - 1] > 0.0 ? 1 : -1;
+}
+
+/* X += s * A * B, s = +1 or -1 (every partial product grown in exactly) */
+static void xp_add_product(xp_t* X, const xp_t* A, const xp_t* B, double s) {
+  for (int a = 0; a < A->n; a++)
+    for (int b = 0; b < B->n; b++) {
+      double p, e;
+      two_prod(A->c[a], B->c[b], &p, &e);
+      xp_grow(X, s * e);
+      xp_grow(X, s * p);
+    }
+  if (A->overflow || B->overflow) X->overflow = 1;
+}
+
+/* exact row (n, 2b) of a plane, recomputed from the sites: n = p_j - p_i,
+ * 2b = |n|^2 + w_i - w_j for site planes, n = +-e_k and 2b = 2 (bound - p)
+ * for box faces (doubling 2b for every plane scales T by 2, not its sign) */
+typedef struct {
+  double nb[3][2], bb[XP_CAP];
+  xp_t N[3], B;
+} xrow_t;
+
+static void exact_row(const problem_t* pr, const plane_t* P, xrow_t* R) {
+  for (int k = 0; k < 3; k++) xp_init(&R->N[k], R->nb[k]);
+  xp_init(&R->B, R->bb);
+  int64_t i = P->owner;
+  if (P->site >= 0) {
+    int64_t j = P->site;
+    for (int k = 0; k < 3; k++) {
+      xp_grow(&R->N[k], site_x(pr, j, k));
+      xp_grow(&R->N[k], -site_x(pr, i, k));
+      xp_add_product(&R->B, &R->N[k], &R->N[k], 1.0);
+    }
+    xp_grow(&R->B, site_w(pr, i));
+    xp_grow(&R->B, -site_w(pr, j));
+  } else {
+    int f = (int)(-1 - P->site), ax = f >> 1;
+    double sg = (f & 1) ? -1.0 : 1.0;
+    xp_grow(&R->N[ax], sg);
+    /* 2 (hi - p) or 2 (p - lo): doubling is exact */
+    if (f & 1) {
+      xp_grow(&R->B, 2.0 * site_x(pr, i, ax));
+      xp_grow(&R->B, -2.0 * pr->lo[ax]);
+    } else {
+      xp_grow(&R->B, 2.0 * pr->hi[ax]);
+      xp_grow(&R->B, -2.0 * site_x(pr, i, ax));
+    }
+  }
+}
+
+/* exact 3x3 determinant of rows r0, r1, r2 whose entries are expansions:
+ * cofactor expansion along r0, each 2x2 minor formed exactly first */
+static void xp_det3(const xp_t* r0[3], const xp_t* r1[3], const xp_t* r2[3], xp_t* D, double* m1) {
+  xp_init(D, D->c);
+  for (int col = 0; col < 3; col++) {
+    int c1 = (col + 1) % 3, c2 = (col + 2) % 3;
+    xp_t M;
+    xp_init(&M, m1);
+    xp_add_product(&M, r1[c1], r2[c2], 1.0);
+    xp_add_product(&M, r1[c2], r2[c1], -1.0);
+    xp_add_product(D, r0[col], &M, 1.0);
+    if (M.overflow) D->overflow = 1;
+  }
+}
+
+/* exact sign of s_v = n_h . v - b_h for the vertex of planes (a, b, c):
+ * sign(T) * sign(D0), with T = n_h . (D1, D2, D3) - b_h D0 and v = D / D0.
+ * Returns +1 / -1, 0 when s_v = 0 or D0 = 0, 2 when an expansion ran out
+ * of room. */
+static int exact_side(const problem_t* pr, const plane_t* Pa, const plane_t* Pb, const plane_t* Pc,
+                      const plane_t* Ph) {
+  xrow_t* R = (xrow_t*)xrealloc(NULL, sizeof(xrow_t) * 4);
+  double* buf = (double*)xrealloc(NULL, sizeof(double) * XP_CAP * 8);
+  exact_row(pr, Pa, &R[0]);
+  exact_row(pr, Pb, &R[1]);
+  exact_row(pr, Pc, &R[2]);
+  exact_row(pr, Ph, &R[3]);
+  const xp_t* rows[3][3];
+  for (int r = 0; r < 3; r++)
+    for (int k = 0; k < 3; k++) rows[r][k] = &R[r].N[k];
+  xp_t D0, Dk, T;
+  xp_init(&D0, buf);
+  xp_det3(rows[0], rows[1], rows[2], &D0, buf + 2 * XP_CAP);
+  xp_init(&T, buf + 4 * XP_CAP);
+  xp_add_product(&T, &R[3].B, &D0, -1.0);
+  for (int k = 0; k < 3; k++) {
+    const xp_t* rk[3][3];
+    for (int r = 0; r < 3; r++)
+      for (int q = 0; q < 3; q++) rk[r][q] = q == k ? &R[r].B : &R[r].N[q];
+    xp_init(&Dk, buf + 5 * XP_CAP);
+    xp_det3(rk[0], rk[1], rk[2], &Dk, buf + 2 * XP_CAP);
+    xp_add_product(&T, &R[3].N[k], &Dk, 1.0);
+  }
+  int over = D0.overflow || T.overflow;
+  for (int r = 0; r < 4; r++) over |= R[r].B.overflow;
+  int sd = xp_sign(&D0), st = xp_sign(&T);
+  free(R);
+  free(buf);
+  if (over) return 2;
+  return sd * st;
+}
+
 /* +1: vertex strictly outside plane H, 0: inside or on it. */
-static int vertex_outside(const vert_t* V, const plane_t* H, int exact, int64_t* stats) {
-  if (exact) {
+static int vertex_outside(const problem_t* pr, const cell_t* C, const vert_t* V, const plane_t* H, int64_t* stats) {
+  if (pr->exact) {
     i128 T = (i128)H->N[0] * V->E[0] + (i128)H->N[1] * V->E[1] + (i128)H->N[2] * V->E[2] -
              (i128)H->B * V->E[3];
     if (T == 0) stats[ST_DEGENERATE]++;
@@ -328,8 +504,15 @@ static int vertex_outside(const vert_t* V, const plane_t* H, int exact, int64_t*
   double bound = 64.0 * EPS *
                  (fabs(H->n[0]) * V->P[0] + fabs(H->n[1]) * V->P[1] + fabs(H->n[2]) * V->P[2] +
                   H->bmag * V->P[3]);
-  if (fabs(T) <= bound) stats[ST_AMBIGUOUS]++;
-  return T > 0.0;
+  if (fabs(T) > bound) return T > 0.0;
+  stats[ST_EXACT]++;
+  int sg = exact_side(pr, &C->pl[V->p[0]], &C->pl[V->p[1]], &C->pl[V->p[2]], H);
+  if (sg == 2) { /* could not certify: keep the FP64 sign and say so */
+    stats[ST_AMBIGUOUS]++;
+    return T > 0.0;
+  }
+  if (sg == 0) stats[ST_DEGENERATE]++;
+  return sg > 0;
 }
 
 /* start the cell as the box (App. B "Initialization", with the user box) */
@@ -377,7 +560,7 @@ static int cell_clip(const problem_t* pr, cell_t* C, const plane_t* H, int64_t* 
   int nv = C->nv, nout = 0;
   /* step 1: classify every vertex */
   for (int k = 0; k < nv; k++) {
-    C->out[k] = vertex_outside(&C->v[k], H, pr->exact, stats);
+    C->out[k] = vertex_outside(pr, C, &C->v[k], H, stats);
     C->removed[k] = 0;
     nout += C->out[k];
   }
@@ -1011,21 +1194,15 @@ static void ibuf_push(ibuf_t* b, int32_t x) {
   b->v[b->n++] = x;
 }
 
-int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi,
-                 const int64_t* cells, int64_t ncells, int mode, int exact, int32_t* counts,
-                 int64_t* offsets, int32_t* nbrs, int64_t nbr_cap, double* vol, double* cen, int32_t* nverts,
-                 int32_t* nfaces, int64_t* stats, int nthreads) {
-  if (n <= 0 || !xyz || !lo || !hi || !counts || !offsets || !vol || !cen || !stats) return ORC_ERR_ARG;
-  problem_t pr;
-  int rc = setup_problem(&pr, xyz, w, n, lo, hi, exact);
-  if (rc) {
-    free_problem(&pr);
-    return rc;
-  }
+/* the cells of one problem whose set-up (and k-d tree, mode 1) is done */
+static int cells_run(const problem_t* prp, const kdtree_t* Tp, int mode, const int64_t* cells, int64_t ncells,
+                     int32_t* counts, int64_t* offsets, int32_t* nbrs, int64_t nbr_cap, double* vol, double* cen,
+                     int32_t* nverts, int32_t* nfaces, int64_t* stats, int nthreads) {
+  const problem_t pr = *prp;
+  const kdtree_t T = *Tp;
+  const float* xyz = pr.xyz;
+  const int64_t n = pr.n;
   if (!cells) ncells = n;
-  kdtree_t T;
-  memset(&T, 0, sizeof(T));
-  if (mode == 1) kd_build(&T, &pr);
   for (int k = 0; k <= ST_N; k++) stats[k] = 0;
   int err = 0;
 #ifdef _OPENMP
@@ -1143,8 +1320,6 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
     free(nb);
     free(tmpn);
   }
-  if (mode == 1) kd_free(&T);
-  free_problem(&pr);
   offsets[0] = 0;
   for (int64_t q = 0; q < ncells; q++) offsets[q + 1] = offsets[q] + (err ? 0 : counts[q]);
   stats[ST_N] = offsets[ncells];
@@ -1159,6 +1334,76 @@ int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, c
   free(where);
   free(owner);
   return err;
+}
+
+int oracle_cells(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi,
+                 const int64_t* cells, int64_t ncells, int mode, int exact, int32_t* counts,
+                 int64_t* offsets, int32_t* nbrs, int64_t nbr_cap, double* vol, double* cen, int32_t* nverts,
+                 int32_t* nfaces, int64_t* stats, int nthreads) {
+  if (n <= 0 || !xyz || !lo || !hi || !counts || !offsets || !vol || !cen || !stats) return ORC_ERR_ARG;
+  problem_t pr;
+  int rc = setup_problem(&pr, xyz, w, n, lo, hi, exact);
+  if (rc) {
+    free_problem(&pr);
+    return rc;
+  }
+  kdtree_t T;
+  memset(&T, 0, sizeof(T));
+  if (mode == 1) kd_build(&T, &pr);
+  rc = cells_run(&pr, &T, mode, cells, ncells, counts, offsets, nbrs, nbr_cap, vol, cen, nverts, nfaces, stats,
+                 nthreads);
+  if (mode == 1) kd_free(&T);
+  free_problem(&pr);
+  return rc;
+}
+
+/*
+ * A session keeps one problem's set-up (duplicate marks, k-d tree) between
+ * calls, so that many samples of cells of one large point set do not each
+ * rebuild the tree. The caller's xyz / w arrays must outlive the session.
+ * oracle_session_cells takes the arguments of oracle_cells from `cells` on.
+ */
+typedef struct {
+  problem_t pr;
+  kdtree_t T;
+  int mode;
+} session_t;
+
+void* oracle_session_open(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi, int mode,
+                          int exact, int* rc) {
+  *rc = ORC_ERR_ARG;
+  if (n <= 0 || !xyz || !lo || !hi) return NULL;
+  session_t* S = (session_t*)calloc(1, sizeof(session_t));
+  if (!S) {
+    *rc = ORC_ERR_MEM;
+    return NULL;
+  }
+  *rc = setup_problem(&S->pr, xyz, w, n, lo, hi, exact);
+  if (*rc) {
+    free_problem(&S->pr);
+    free(S);
+    return NULL;
+  }
+  S->mode = mode;
+  if (mode == 1) kd_build(&S->T, &S->pr);
+  return S;
+}
+
+int oracle_session_cells(void* h, const int64_t* cells, int64_t ncells, int32_t* counts, int64_t* offsets,
+                         int32_t* nbrs, int64_t nbr_cap, double* vol, double* cen, int32_t* nverts, int32_t* nfaces,
+                         int64_t* stats, int nthreads) {
+  session_t* S = (session_t*)h;
+  if (!S || !counts || !offsets || !vol || !cen || !stats) return ORC_ERR_ARG;
+  return cells_run(&S->pr, &S->T, S->mode, cells, ncells, counts, offsets, nbrs, nbr_cap, vol, cen, nverts, nfaces,
+                   stats, nthreads);
+}
+
+void oracle_session_close(void* h) {
+  session_t* S = (session_t*)h;
+  if (!S) return;
+  if (S->mode == 1) kd_free(&S->T);
+  free_problem(&S->pr);
+  free(S);
 }
 
 /*
@@ -1380,7 +1625,7 @@ int oracle_certify(const float* xyz, const float* w, int64_t n, const float* lo,
             continue;
           plane_t P;
           make_site_plane(&pr, i, mm, &P);
-          if (vertex_outside(&C.v[k], &P, exact, st)) out_viol[q]++;
+          if (vertex_outside(&pr, &C, &C.v[k], &P, st)) out_viol[q]++;
         }
     }
 #pragma omp critical
@@ -1549,6 +1794,37 @@ int oracle_fd_grad(const float* xyz, const float* w, int64_t n, const float* lo,
   }
   free_problem(&base);
   return err;
+}
+
+/*
+ * oracle_exact_side: the exact sign, from the expansion arithmetic above, of
+ * s_v = n_h . v - b_h where v is the vertex of the planes of ids[0..2] in the
+ * frame of site i and h the plane of ids[3] (ids: site index, or -1-f for
+ * box face f). Returns +1, -1, 0 (s_v = 0 or the three planes are
+ * dependent), 2 (no room), or ORC_ERR_ARG. A testing entry point.
+ */
+int oracle_exact_side(const float* xyz, const float* w, int64_t n, const float* lo, const float* hi, int64_t i,
+                      const int64_t* ids) {
+  if (n <= 0 || !xyz || !lo || !hi || !ids || i < 0 || i >= n) return ORC_ERR_ARG;
+  problem_t pr;
+  memset(&pr, 0, sizeof(pr));
+  pr.ov_site = -1;
+  pr.xyz = xyz;
+  pr.w = w;
+  pr.n = n;
+  for (int k = 0; k < 3; k++) {
+    pr.lo[k] = lo[k];
+    pr.hi[k] = hi[k];
+  }
+  plane_t P[4];
+  for (int k = 0; k < 4; k++) {
+    if (ids[k] >= n || ids[k] < -6 || ids[k] == i) return ORC_ERR_ARG;
+    if (ids[k] >= 0)
+      make_site_plane(&pr, i, ids[k], &P[k]);
+    else
+      make_box_plane(&pr, i, (int)(-1 - ids[k]), &P[k]);
+  }
+  return exact_side(&pr, &P[0], &P[1], &P[2], &P[3]);
 }
 
 int oracle_stat_count(void) { return ST_N; }

@@ -192,6 +192,130 @@ def test_exact_predicates_agree_and_certify(weighted):
     assert viol.sum() == 0 and st["degenerate"] == 0
 
 
+def _rational_side(x, w, box, i, ids):
+    """Sign of pow(v, i) - pow(v, h) (Eq. 1: positive means v lies outside
+    the half-space of h) for the vertex v where the three planes of ids[:3]
+    meet, all in exact rational arithmetic from the float32 inputs; box face
+    f bounds the cell by the box side it names."""
+    from fractions import Fraction as F
+
+    P = [[F(float(c)) for c in x[k]] for k in range(len(x))]
+    Wt = [F(float(c)) for c in (w if w is not None else np.zeros(len(x)))]
+    lo = [F(float(c)) for c in box[0]]
+    hi = [F(float(c)) for c in box[1]]
+
+    def row(j):  # a . X = r in world coordinates X
+        if j >= 0:
+            a = [2 * (P[j][k] - P[i][k]) for k in range(3)]
+            r = sum(P[j][k] ** 2 - P[i][k] ** 2 for k in range(3)) + Wt[i] - Wt[j]
+            return a, r
+        f = -1 - j
+        ax = f >> 1
+        a = [F(0)] * 3
+        a[ax] = F(-1) if f & 1 else F(1)
+        return a, (-lo[ax] if f & 1 else hi[ax])
+
+    A, r = zip(*[row(j) for j in ids[:3]])
+
+    def det(m):
+        return (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+                + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+
+    D = det(A)
+    if D == 0:
+        return 0
+    X = []
+    for k in range(3):
+        m = [list(a) for a in A]
+        for q in range(3):
+            m[q][k] = r[q]
+        X.append(det(m) / D)
+    h = ids[3]
+    if h >= 0:
+        pi = sum((X[k] - P[i][k]) ** 2 for k in range(3)) - Wt[i]
+        ph = sum((X[k] - P[h][k]) ** 2 for k in range(3)) - Wt[h]
+        d = pi - ph
+    else:
+        f = -1 - h
+        ax = f >> 1
+        d = (lo[ax] - X[ax]) if f & 1 else (X[ax] - hi[ax])
+    return (d > 0) - (d < 0)
+
+
+def test_exact_side_matches_rational_arithmetic():
+    """The expansion arithmetic behind the oracle's exact fallback against
+    exact rationals (Python fractions) on random, exactly degenerate and
+    near-degenerate configurations, Voronoi and power, with box faces."""
+    rng = W.rng_for(5)
+    box = ((0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    counts = {-1: 0, 0: 0, 1: 0}
+    for t in range(320):
+        kind = t % 4 if t < 240 else 4 + t % 2
+        if kind == 0:  # generic
+            x = rng.random((5, 3)).astype(np.float32)
+        elif kind >= 4:
+            # five sites at sign / permutation images of one offset d about a
+            # centre c (all at |d| from c), d with 21 random bits per axis:
+            # exactly degenerate, but the determinants' products need more
+            # than 53 bits (kind 5: the last site one ulp off the sphere)
+            d = (rng.integers(2 ** 20, 2 ** 21, 3) * 2.0 ** -24).astype(np.float64)
+            imgs = [(0, 1, 2, 1, 1, 1), (1, 2, 0, -1, 1, 1), (2, 0, 1, 1, -1, 1), (0, 2, 1, 1, 1, -1),
+                    (2, 1, 0, -1, -1, 1)]
+            x = np.array([[0.5 + sx * d[a], 0.5 + sy * d[b], 0.5 + sz * d[c_]] for a, b, c_, sx, sy, sz in imgs],
+                         np.float64)
+            assert np.all(x.astype(np.float32).astype(np.float64) == x)
+            x = x.astype(np.float32)
+            if kind == 5:
+                k = int(rng.integers(0, 3))
+                x[4, k] = np.nextafter(x[4, k], np.float32(2.0 if t % 4 == 1 else -2.0))
+        elif kind == 1:  # five sites on one sphere: exactly degenerate
+            c = rng.integers(8, 24, 3)
+            pts = [c + np.array(v) for v in ((3, 0, 0), (-3, 0, 0), (0, 3, 0), (0, 0, -3), (0, -3, 0))]
+            x = (np.array(pts, np.float64) / 32.0).astype(np.float32)
+        else:  # one site moved by one float32 ulp off a common sphere
+            c = rng.integers(8, 24, 3)
+            pts = [c + np.array(v) for v in ((3, 0, 0), (-3, 0, 0), (0, 3, 0), (0, 0, -3), (0, -3, 0))]
+            x = (np.array(pts, np.float64) / 32.0).astype(np.float32)
+            k = int(rng.integers(0, 3))
+            x[4, k] = np.nextafter(x[4, k], np.float32(2.0 if kind == 2 else -2.0))
+        w = None
+        if t % 8 >= 4:  # power: equal weights keep the sphere; others perturb it
+            w = np.full(5, 0.001, np.float32) if kind in (1, 4) else (rng.random(5) * 1e-3).astype(np.float32)
+        ids = [1, 2, 3, 4]
+        if t % 5 == 0 and kind < 4:
+            ids = [1, 2, -1 - int(rng.integers(0, 6)), 4]  # a box face among the three planes
+        got = oracle.exact_side(x, w, box, 0, ids)
+        want = _rational_side(x, w, box, 0, ids)
+        assert got == want, (t, got, want)
+        counts[want] += 1
+    assert counts[0] >= 40 and counts[1] >= 20 and counts[-1] >= 20
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_fp64_with_exact_fallback_equals_integer_mode_on_degenerate_lattices(weighted):
+    """On a cubic and a BCC lattice (five or more cospherical sites
+    everywhere: many predicates exactly 0) the FP64 filter cannot decide;
+    its exact fallback must take exactly the decisions of the integer mode,
+    so every cell is the same."""
+    # spacing: 17 random bits on the 2^-20 grid, so that the integer mode
+    # applies and the FP64 determinants round (their products pass 53 bits)
+    a = int(W.rng_for(8).integers(2 ** 16, 2 ** 17)) * 2.0 ** -20
+    k = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    cube = 0.25 + k * a
+    bcc = np.concatenate([cube, 0.25 + (k[:125] + 0.5) * a])
+    assert np.all(np.round(bcc * 2 ** 20) == bcc * 2 ** 20)
+    for pts in (cube, bcc):
+        x = pts.astype(np.float32)
+        w = np.full(len(x), 2.0 ** -10, np.float32) if weighted else None
+        e = oracle.cells(x, w, exact=True)
+        f = oracle.cells(x, w, exact=False)
+        assert e["stats"]["degenerate"] > 0
+        assert f["stats"]["exact_resolved"] > 0 and f["stats"]["ambiguous"] == 0
+        assert f["stats"]["degenerate"] == e["stats"]["degenerate"]
+        assert all(np.array_equal(p, q) for p, q in zip(e["nbrs"], f["nbrs"]))
+        np.testing.assert_allclose(f["vol"], e["vol"], rtol=1e-12, atol=1e-15)
+
+
 # ---------------------------------------------------------------- library cross-checks
 
 def test_voronoi_neighbours_equal_qhull_delaunay_edges():
