@@ -96,10 +96,14 @@ typedef struct {
   int32_t blocks_per_sm;   /* persistent kernel grid = SMs * this (0 = occupancy)    */
   int32_t counters;        /* 1: count tests, clips and nodes (small overhead)       */
   int32_t timing;          /* 1: record CUDA events around each phase (vd_get_timings)*/
-  int32_t warm_start;      /* 1: clip each cell first with its 32 Morton-order       */
-                           /*    neighbours (App. A.6 warm start, without KNN);     */
-                           /*    default 0 (best-first reaches that leaf first);    */
-                           /*    warp-per-cell form only                            */
+  int32_t warm_start;      /* warm start of App. A.6: each cell is first clipped by */
+                           /*    1: its 32 Morton-order neighbours (one coalesced   */
+                           /*       load, no extra pass), or                        */
+                           /*    2: its 8 nearest sites (KNN, found by a query on   */
+                           /*       the LBVH before the cells are built);           */
+                           /*    then the traversal skips them. Default 0 (the      */
+                           /*    best-first traversal reaches the nearest leaf      */
+                           /*    first); warp-per-cell form only                    */
   int32_t cell_mode;       /* 0: one warp per cell, polytope in registers (default);*/
                            /* 1: one thread per cell, polytope in per-thread memory */
                            /*    (the paper's mapping, App. A.3: 64 vertices, 48    */
@@ -138,7 +142,9 @@ typedef struct {
   int64_t failed_cells;       /* cells that overflowed even the large capacity      */
   int64_t fp64_fallbacks;     /* FP32 predicates re-evaluated in FP64               */
   int64_t fp64_ambiguous;     /* FP64 re-evaluations still inside their error bound */
-  int64_t candidates;         /* counters=1: candidate planes tested on vertices    */
+  int64_t candidates;         /* counters=1: candidate planes tested on vertices,   */
+                              /*   main pass (fused kernel) only; the large-cell    */
+                              /*   pass counts in the large_* fields below          */
   int64_t clips;              /* counters=1: clips that removed vertices            */
   int64_t nodes;              /* counters=1: BVH nodes tested                       */
   int64_t vertex_tests;       /* counters=1: vertex-plane sign tests                */
@@ -147,6 +153,18 @@ typedef struct {
   int64_t refined_volumes;    /* cells whose volume/centroid were integrated in FP64 */
   int64_t overflow_reason[4]; /* register-path overflows by cause: queue, vertices,  */
                               /*   planes, neighbours (> 64 per row)                */
+  int64_t large_candidates;   /* counters=1: the same five counts for the           */
+  int64_t large_clips;        /*   large-cell pass (cells that left the register    */
+  int64_t large_nodes;        /*   path), including the vertex tests its helping    */
+  int64_t large_vertex_tests; /*   warps ran                                        */
+  int64_t large_new_vertices;
+  int64_t large_tape_records; /* large-cell polytopes the forward kept on the       */
+                              /*   large-cell tape (vd_config.tape)                 */
+  int64_t large_tape_restored;/* ... restored from it by the last vd_backward /     */
+                              /*   vd_backward_mesh (the others were re-clipped)    */
+  int64_t ambiguous_cells;    /* cells of the last build that took at least one     */
+                              /*   FP64 sign still inside its FP64 error bound      */
+                              /*   (their ids: vd_ambiguous_cells)                  */
 } vd_status;
 
 /* Per-phase device times of the last call, from CUDA events recorded on the
@@ -181,6 +199,22 @@ int vd_destroy(vd_ctx* ctx);
 
 /* Replace the context's configuration (same validation as vd_create). */
 int vd_set_config(vd_ctx* ctx, const vd_config* cfg);
+
+/* Partition of one diagram's cells over several contexts (typically one
+ * per GPU; a project addition: the paper is single-GPU, and Sec. 3's cells
+ * are independent). After vd_set_partition(ctx, part, nparts), every build
+ * of ctx still sorts all n sites and builds the whole LBVH (each part holds
+ * a replica), but makes only the cells of sorted (Morton-order) indices
+ * [floor(part n / nparts), floor((part + 1) n / nparts)); every other cell
+ * gets an empty neighbour row and volume and centroid 0, so that summing
+ * the parts' volume and centroid arrays, and concatenating their rows,
+ * gives the whole diagram. vd_backward / vd_backward_mesh / vd_cells_mesh
+ * then cover only this part's cells: the parts' gradients sum to the
+ * whole gradient. The sort is deterministic, so parts built from the same
+ * input on different devices are disjoint and cover every cell.
+ * nparts = 1 (the default) builds every cell.
+ * Errors: VD_ERR_INVALID_ARG unless 0 <= part < nparts. */
+int vd_set_partition(vd_ctx* ctx, int32_t part, int32_t nparts);
 
 /* Pre-size the workspace for up to n sites (synchronous allocation), so
  * that later builds of at most n sites allocate nothing and can be
@@ -252,6 +286,20 @@ int vd_get_timings(vd_ctx* ctx, vd_timings* t);
 
 /* Synchronise the context's last stream and copy its device-side status. */
 int vd_get_status(vd_ctx* ctx, vd_status* st);
+
+/* The cells of the last forward build whose construction took an FP64 sign
+ * test that was still inside its FP64 error bound (the "fp64_ambiguous"
+ * events of vd_status, by cell), so that a caller can check exactly those
+ * cells against exact arithmetic (a project addition: the paper runs FP32
+ * only and reports no such set). Synchronises the context's last stream.
+ *   cells    : HOST int64 [capacity]: original site indices (global indices
+ *              for batched builds), in no particular order; a cell re-run by
+ *              the large-cell pass may appear twice.
+ *   capacity : entries `cells` holds (0 with cells = NULL: count only).
+ *   count    : HOST scalar: how many were recorded; at most the first 65,536
+ *              are kept, so count > 65,536 means the list is truncated.
+ * Errors: VD_ERR_INVALID_ARG, VD_ERR_NO_FORWARD, VD_ERR_CUDA. */
+int vd_ambiguous_cells(vd_ctx* ctx, int64_t* cells, int64_t capacity, int64_t* count);
 
 /* Static string for a VD_* code (never NULL). */
 const char* vd_error_string(int code);
@@ -326,32 +374,39 @@ int vd_autotune_batched(vd_ctx* ctx, const float* sites_xyz, const float* weight
 #define VD_NOALLOC_MAX_SITES 16384 /* sites per call                          */
 #define VD_NOALLOC_ROW 64          /* neighbour slots per cell in `neighbors` */
 
-/* Cells of one small point set without allocating any device memory. There
- * is no counterpart in the paper, whose pipeline allocates its buffers; this
- * exists for callers that cannot call cudaMalloc (code running under another
- * framework's allocator or memory pool, loops that forbid allocation after
- * start-up, callers that must not create a context workspace).
+/* Cells of one small point set without allocating any device memory. The
+ * paper has no counterpart: its pipeline allocates its buffers. This entry
+ * point exists for callers that cannot call cudaMalloc: code that runs under
+ * another framework's allocator or memory pool (whose accounting a private
+ * allocation would bypass), real-time or safety-critical loops that forbid
+ * allocation once they have started, and callers that must not create a
+ * context with its workspace.
  *
- * Same cells as vd_build (Eq. 1 clipped to bbox; every other site is a
- * candidate, culled by the same bounds), written into caller buffers:
+ * The cells are those vd_build computes (same clipping, same culling tests,
+ * same duplicate rule), for one set with every other site a candidate,
+ * written into the caller's buffers:
  *   sites_xyz : DEVICE float32 [3n];  weights : DEVICE float32 [n] or NULL.
  *   n         : 1 <= n <= VD_NOALLOC_MAX_SITES, else VD_ERR_TOO_LARGE.
- *   counts    : DEVICE int32 [n]: neighbour count of each cell (-1 when the
- *               cell exceeded the register capacity or VD_NOALLOC_ROW).
+ *   counts    : DEVICE int32 [n]: neighbour count of each cell, or -1 when
+ *               the cell outgrew the register capacity or has more than
+ *               VD_NOALLOC_ROW neighbours (its volume and centroid are then
+ *               NaN and the status word is VD_ERR_CELL_OVERFLOW).
  *   neighbors : DEVICE int32 [n * VD_NOALLOC_ROW]: row i holds counts[i]
  *               ascending neighbour indices (the rest is left unwritten).
  *   volume    : DEVICE float32 [n];  centroid : DEVICE float32 [3n].
  *   status    : DEVICE int32 scalar: VD_OK, VD_ERR_INVALID_ARG (non-finite
  *               input) or VD_ERR_CELL_OVERFLOW.
- * Scratch: a fixed file-scope device array (about 272 KB) that every GPU
- * loading the library holds until exit. Its device address is looked up on
- * the first call on each device (with that device current), so make that
- * first call before any stream capture. All calls share the array and it
- * keeps the last call's contents (the work counter and error word are
- * cleared on every call): calls that overlap on the GPU (different streams
- * or devices' threads racing on one device) race on it and must be
- * serialised by the caller. Returns VD_OK / VD_ERR_INVALID_ARG /
- * VD_ERR_TOO_LARGE / VD_ERR_CUDA. */
+ * Scratch: one fixed file-scope device array (about 272 KB) that every GPU
+ * loading the library holds until the process exits. Its device address is
+ * looked up on the first call on each device (with that device current),
+ * and again on the first call after a cudaDeviceReset of that device: make
+ * those calls before any stream capture. Every call shares the array and it
+ * keeps the last call's contents (the work counter and the error word are
+ * cleared on every call): calls that overlap on the GPU (two streams, or two
+ * host threads on one device) race on it, so the caller must serialise them.
+ * Returns VD_OK, VD_ERR_INVALID_ARG, VD_ERR_TOO_LARGE or VD_ERR_CUDA (a
+ * launch of this call failed; an error left by earlier work of the caller is
+ * neither reported nor cleared). */
 int vd_cells_noalloc(const float* sites_xyz, const float* weights, int64_t n, vd_box bbox, int32_t* counts,
                      int32_t* neighbors, float* volume, float* centroid, int32_t* status, void* stream);
 

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libvd.so")
-SOURCES = ["vd_api.cu", "vd_bvh.cu", "vd_cells.cu", "vd_thread.cu", "vd_csr.cu", "vd_backward.cu", "vd_noalloc.cu"]
+SOURCES = ["vd_api.cu", "vd_bvh.cu", "vd_cells.cu", "vd_thread.cu", "vd_csr.cu", "vd_backward.cu", "vd_noalloc.cu",
+           "vd_knn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -19,6 +19,7 @@ using namespace vd;
 namespace {
 
 constexpr int kStride = 64;      // neighbour row stride of the register-resident pass
+constexpr int kAmbCap = 1 << 16; // cells recorded with an FP64-ambiguous sign test
 constexpr int kHistEntries = 256 * 2 * kSortBlocksMax;
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -74,6 +75,8 @@ struct vd_ctx {
   int* ovf_slot = nullptr;
   int* blist = nullptr;
   int* vcount = nullptr;  // mesh output: vertices per cell
+  int* amb_list = nullptr;  // cells with an FP64-ambiguous sign test (last forward)
+  int* knn = nullptr;       // KNN warm start: kKnn nearest sites of every sorted site
   long long* block_sums = nullptr;
   int* work = nullptr;  // [8] work counters
   unsigned* wrange = nullptr;  // [2] orderable min / max weight
@@ -107,6 +110,11 @@ struct vd_ctx {
   int64_t btape_cap = 0;
   // autotuner: best configuration per (log2 n, weighted, set count)
   std::map<std::tuple<int, int, int>, vd_config> tuned;
+  // partition of the cells (vd_set_partition): this context builds part
+  // `part` of `nparts` contiguous ranges of the Morton-sorted order
+  int part = 0;
+  int nparts = 1;
+  int last_begin = 0, last_end = 0;  // the range of the last forward build
 };
 
 // events 0..6 bracket the phases: pack | sort | bvh | cells | overflow | csr
@@ -134,7 +142,7 @@ static int check_config(const vd_config* c) {
   if (c->warps_per_block < 1 || c->warps_per_block > 8) return VD_ERR_INVALID_ARG;
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64) return VD_ERR_INVALID_ARG;
   if (c->counters < 0 || c->counters > 1 || c->timing < 0 || c->timing > 1) return VD_ERR_INVALID_ARG;
-  if (c->warm_start < 0 || c->warm_start > 1) return VD_ERR_INVALID_ARG;
+  if (c->warm_start < 0 || c->warm_start > 2) return VD_ERR_INVALID_ARG;
   if (c->cell_mode < 0 || c->cell_mode > 1) return VD_ERR_INVALID_ARG;
   if (c->precision < 0 || c->precision > 1) return VD_ERR_INVALID_ARG;
   if (c->tape < 0 || c->tape > 1) return VD_ERR_INVALID_ARG;
@@ -189,6 +197,8 @@ static Layout make_layout(int64_t n, int num_sms) {
   L.add(big_arena_bytes() * (size_t)big_warps(num_sms));  // 25 arenas
   L.add((size_t)n);                    // 26 duplicate losers
   L.add(sizeof(int) * n);              // 27 mesh vertex count per cell
+  L.add(sizeof(int) * kAmbCap);        // 28 cells with an FP64-ambiguous sign test
+  L.add(sizeof(int) * kKnn * (size_t)n);  // 29 KNN warm start: nearest sites per site
   return L;
 }
 
@@ -270,6 +280,8 @@ static int reserve(vd_ctx* ctx, int64_t n) {
   ctx->arena = b + L.off[25];
   ctx->loser = (unsigned char*)(b + L.off[26]);
   ctx->vcount = (int*)(b + L.off[27]);
+  ctx->amb_list = (int*)(b + L.off[28]);
+  ctx->knn = (int*)(b + L.off[29]);
   ctx->ovf_list = (int*)(b + L.off[18]);
   ctx->ovf_slot = (int*)(b + L.off[19]);
   ctx->blist = (int*)(b + L.off[20]);
@@ -310,6 +322,11 @@ static CellBuffers cell_buffers(vd_ctx* ctx) {
   c.stall = ctx->test_stall ? ctx->work + 6 : nullptr;
   c.btape = c.tape ? ctx->btape : nullptr;
   c.btape_cap = c.tape ? ctx->btape_cap : 0;
+  c.amb_list = ctx->amb_list;
+  c.amb_cap = kAmbCap;
+  c.cell_begin = ctx->last_begin;
+  c.cell_end = ctx->last_end;
+  c.knn = ctx->knn;
   return c;
 }
 
@@ -388,13 +405,26 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   b.nodes = ctx->nodes;
   e = launch_build_bvh(ctx->keys_sorted, ctx->sites, n, ctx->cfg.leaf_size, b, ctx->sets_dev, nsets, ctx->st, s);
   if (e != cudaSuccess) return VD_ERR_CUDA;
-  // 5. fused traversal + cull + clip (Alg. 1, Sec. 4, App. B)
+  // 5. fused traversal + cull + clip (Alg. 1, Sec. 4, App. B), over this
+  // context's part of the sorted order; the other cells get no neighbours
+  // and volume / centroid 0
   ctx->last_n = n;
   ctx->last_nsets = nsets;
   ctx->set_shift = set_shift;
+  ctx->last_begin = (int)(((int64_t)n * ctx->part) / ctx->nparts);
+  ctx->last_end = (int)(((int64_t)n * (ctx->part + 1)) / ctx->nparts);
+  if (ctx->nparts > 1) {
+    cudaMemsetAsync(out->volume, 0, sizeof(float) * (size_t)n, s);
+    cudaMemsetAsync(out->centroid, 0, sizeof(float) * 3 * (size_t)n, s);
+  }
   CellBuffers c = cell_buffers(ctx);
   c.vol = out->volume;
   c.cen = out->centroid;
+  const bool knn = ctx->cfg.warm_start == 2 && ctx->cfg.cell_mode == 0;
+  if (knn) {  // the KNN warm start's lists (App. A.6), for this build's cells
+    e = launch_knn(c, ctx->knn, s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+  }
   mark(ctx, 3, s);
   e = launch_cells(c, ctx->num_sms, s, [&]() { mark(ctx, 4, s); });
   if (e != cudaSuccess) return VD_ERR_CUDA;
@@ -411,7 +441,7 @@ static int run_forward(vd_ctx* ctx, const float* xyz, const float* w, int n, int
   ctx->ev_backward = false;
   int passes = (bits + 7) / 8;
   ctx->launches = (w ? 1 : 0) + 1 + 3 * passes + 3 + (n >= 2 ? 4 : 1) + 2 + 3 +
-                  (out->neighbors && out->nnz_capacity > 0) + 1;
+                  (out->neighbors && out->nnz_capacity > 0) + 1 + (knn ? 1 : 0);
   return VD_OK;
 }
 
@@ -481,6 +511,13 @@ int vd_set_config(vd_ctx* ctx, const vd_config* cfg) {
   int rc = check_config(cfg);
   if (rc) return rc;
   ctx->cfg = *cfg;
+  return VD_OK;
+}
+
+int vd_set_partition(vd_ctx* ctx, int32_t part, int32_t nparts) {
+  if (!ctx || nparts < 1 || part < 0 || part >= nparts) return VD_ERR_INVALID_ARG;
+  ctx->part = part;
+  ctx->nparts = nparts;
   return VD_OK;
 }
 
@@ -584,6 +621,7 @@ static int backward_common(vd_ctx* ctx, const float* grad_volume, const float* g
   cudaMemsetAsync(grad_sites, 0, sizeof(float) * 3 * (size_t)n, s);
   if (grad_weights) cudaMemsetAsync(grad_weights, 0, sizeof(float) * (size_t)n, s);
   cudaMemsetAsync(&ctx->st->error, 0, sizeof(int), s);
+  cudaMemsetAsync(&ctx->st->btape_restored, 0, sizeof(long long), s);
   BackBuffers b;
   std::memset(&b, 0, sizeof(b));
   b.gvol = grad_volume;
@@ -707,7 +745,35 @@ int vd_get_status(vd_ctx* ctx, vd_status* st) {
   st->refined_vertices = d.refined_vertices;
   st->refined_volumes = d.refined_volumes;
   for (int k = 0; k < 4; k++) st->overflow_reason[k] = d.ovf_reason[k];
+  st->large_candidates = d.large_candidates;
+  st->large_clips = d.large_clips;
+  st->large_nodes = d.large_nodes;
+  st->large_vertex_tests = d.large_vtests;
+  st->large_new_vertices = d.large_newv;
+  st->large_tape_records = d.btape_records;
+  st->large_tape_restored = d.btape_restored;
+  st->ambiguous_cells = d.amb_count;
   return VD_OK;
+}
+
+int vd_ambiguous_cells(vd_ctx* ctx, int64_t* cells, int64_t capacity, int64_t* count) {
+  if (!ctx || !count || capacity < 0 || (capacity > 0 && !cells)) return VD_ERR_INVALID_ARG;
+  *count = 0;
+  if (!ctx->st || !ctx->have_forward) return VD_ERR_NO_FORWARD;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return VD_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return VD_ERR_CUDA;
+  int total = 0;
+  if (cudaMemcpy(&total, &ctx->st->amb_count, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VD_ERR_CUDA;
+  *count = total;
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(total, kAmbCap), capacity);
+  if (m <= 0) return VD_OK;
+  int* tmp = new (std::nothrow) int[m];
+  if (!tmp) return VD_ERR_CUDA;
+  cudaError_t e = cudaMemcpy(tmp, ctx->amb_list, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost);
+  for (int64_t k = 0; k < m; k++) cells[k] = tmp[k];
+  delete[] tmp;
+  return e == cudaSuccess ? VD_OK : VD_ERR_CUDA;
 }
 
 }  // extern "C"
@@ -804,7 +870,7 @@ static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::
     const Knob knobs[] = {
         {&vd_config::cell_mode, {0, 1, 0}, 2, false},  {&vd_config::verts_per_lane, {2, 4, 0}, 2, true},
         {&vd_config::queue_per_lane, {2, 4, 8}, 3, true}, {&vd_config::leaf_size, {8, 16, 32}, 3, false},
-        {&vd_config::warps_per_block, {2, 4, 8}, 3, true}, {&vd_config::warm_start, {0, 1, 0}, 2, true},
+        {&vd_config::warps_per_block, {2, 4, 8}, 3, true}, {&vd_config::warm_start, {0, 1, 2}, 3, true},
     };
     for (const Knob& k : knobs) {
       if (k.warp_only && cur.cell_mode != 0) continue;

@@ -377,8 +377,8 @@ __global__ void back_kernel(BackBuffers B) {
   while (true) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&B.work[0], 1);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= B.c.n) break;
+    item = __shfl_sync(FULL, item, 0) + B.c.cell_begin;
+    if (item >= B.c.cell_end) break;
     if (!back_cell<VPL, PCAP, QPL>(B, S, item) && lane == 0) {
       int k = atomicAdd(B.list_count, 1);
       if (k < B.list_cap)
@@ -465,7 +465,9 @@ __device__ bool big_back_cell(const BackBuffers& B, const BigArena& A, int si, C
   if (cnt <= 0) return true;
   // the forward's polytope from the large-cell tape, else re-clipped from
   // the cell's neighbour row
-  if (!(B.tape && big_tape_read(c, A, B, si))) {
+  const bool restored = B.tape && big_tape_read(c, A, B, si);
+  if (restored && lane == 0) atomicAdd((unsigned long long*)&P.st->btape_restored, 1ull);
+  if (!restored) {
     big_init(c, A, 0);
     const int slot = P.ovf_slot[orig_i];
     const int* row = slot >= 0 ? P.pool + slot : P.scratch + (size_t)orig_i * P.stride;

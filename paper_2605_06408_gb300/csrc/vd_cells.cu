@@ -32,10 +32,21 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
                             const CellBuffers& P, int skip0, int skip1) {
   const unsigned lane = lane_id();
   const bool counters = P.cfg.counters != 0;
-  int first = leaf_first(ref), cnt = leaf_count(ref);
-  int j = first + (int)lane;
-  // sites of the warm-start window [skip0, skip1) were clipped already
-  bool act = (int)lane < cnt && j != si && (j < skip0 || j >= skip1);
+  int j;
+  bool act;
+  if (ref == kKnnLeaf) {  // the KNN warm start: the cell's nearest sites
+    j = (int)lane < kKnn ? S.knn[lane] : -1;
+    act = j >= 0;
+  } else {
+    const int first = leaf_first(ref), cnt = leaf_count(ref);
+    j = first + (int)lane;
+    // sites of the warm-start window [skip0, skip1) were clipped already
+    act = (int)lane < cnt && j != si && (j < skip0 || j >= skip1);
+    if (P.cfg.warm_start == 2) {  // and so were the KNN sites
+#pragma unroll
+      for (int k = 0; k < kKnn; k++) act = act && S.knn[k] != j;
+    }
+  }
   if (act) act = P.loser[j] == 0;
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) q = P.sites[j];
@@ -73,9 +84,10 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
     Hb.nz = __shfl_sync(FULL, H.nz, src);
     Hb.b = __shfl_sync(FULL, H.b, src);
     Hb.e = __shfl_sync(FULL, H.e, src);
+    const int hj = __shfl_sync(FULL, j, src);
     if ((int)lane == src) keep = false;
     km &= ~(1u << src);
-    int rc = clip_cell(c, S, Hb, first + src, P.sites, counters);
+    int rc = clip_cell(c, S, Hb, hj, P.sites, counters);
     if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW || rc == CLIP_OVF_PLANES) return rc;
     if (rc == CLIP_DONE) {
       c.dirty = true;
@@ -293,7 +305,11 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   int skip0 = 0, skip1 = 0;
   bool warm = P.cfg.warm_start != 0;
   int cur = SI.root;
-  if (warm) {
+  if (P.cfg.warm_start == 2) {  // KNN warm start (App. A.6): the list of this cell
+    if (lane < kKnn) S.knn[lane] = P.knn[(size_t)si * kKnn + lane];
+    __syncwarp();
+    cur = kKnnLeaf;
+  } else if (warm) {
     const int lo = SI.first, hi = SI.first + SI.count;
     skip0 = max(lo, min(si - 16, hi - 32));
     skip1 = min(hi, skip0 + 32);
@@ -436,12 +452,12 @@ __device__ inline void flush_counters(const CellBuffers& P, const Counters& ct, 
     if (f64a) atomicAdd((unsigned long long*)&P.st->fp64_ambiguous, (unsigned long long)f64a);
     if (rv) atomicAdd((unsigned long long*)&P.st->refined_vertices, (unsigned long long)rv);
     if (ct.refvol) atomicAdd((unsigned long long*)&P.st->refined_volumes, (unsigned long long)ct.refvol);
-    if (P.cfg.counters) {
-      atomicAdd((unsigned long long*)&P.st->candidates, (unsigned long long)ct.cand);
-      atomicAdd((unsigned long long*)&P.st->clips, (unsigned long long)ct.clips);
-      atomicAdd((unsigned long long*)&P.st->nodes, (unsigned long long)ct.nodes);
-      atomicAdd((unsigned long long*)&P.st->vertex_tests, (unsigned long long)ct.vtests);
-      atomicAdd((unsigned long long*)&P.st->new_vertices, (unsigned long long)ct.newv);
+    if (P.cfg.counters) {  // the large-cell pass counts apart from the main pass
+      atomicAdd((unsigned long long*)&P.st->large_candidates, (unsigned long long)ct.cand);
+      atomicAdd((unsigned long long*)&P.st->large_clips, (unsigned long long)ct.clips);
+      atomicAdd((unsigned long long*)&P.st->large_nodes, (unsigned long long)ct.nodes);
+      atomicAdd((unsigned long long*)&P.st->large_vtests, (unsigned long long)ct.vtests);
+      atomicAdd((unsigned long long*)&P.st->large_newv, (unsigned long long)ct.newv);
     }
   }
 }
@@ -489,12 +505,18 @@ __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
     int item = 0;
     if (lane == 0) item = atomicAdd(&P.work[0], 1);
     item = __shfl_sync(FULL, item, 0);
-    if (item >= P.n) break;
-    const int si = item;
+    const int si = P.cell_begin + item;
+    if (si >= P.cell_end) break;
     const int orig = P.perm[si];
     int* row = P.scratch + (size_t)orig * P.stride;
     int reason = 0;
-    if (!build_cell<VPL, PCAP, QPL>(P, S, si, row, empties, reason)) {
+    // the ambiguous-sign count before the cell, kept in shared memory (not
+    // a register live across the whole build)
+    if (lane == 0) S.amb_mark = S.ct.fp64amb;
+    const bool built = build_cell<VPL, PCAP, QPL>(P, S, si, row, empties, reason);
+    __syncwarp();
+    if (lane == 0 && S.ct.fp64amb != S.amb_mark) record_ambiguous(P.st, P.amb_list, P.amb_cap, orig);
+    if (!built) {
       overflows++;
       if (P.tape && lane == 0) *reinterpret_cast<int4*>(P.tape + (size_t)si * kTapeStride) = make_int4(-1, 0, 0, 0);
       if (lane == 0) atomicAdd((unsigned long long*)&P.st->ovf_reason[reason], 1ull);
@@ -745,6 +767,7 @@ __device__ inline void big_tape_write(const BigCell& c, const BigArena& A, const
   }
   for (int p = (int)lane; p < c.npl; p += 32) pid[p] = A.pid[p];
   if (lane == 0) {
+    atomicAdd((unsigned long long*)&P.st->btape_records, 1ull);
     *reinterpret_cast<int4*>(rec) = make_int4(c.nv, c.npl, 0, 0);
     *reinterpret_cast<int4*>(P.tape + (size_t)si * kTapeStride) =
         make_int4(-2, c.npl, (int)(unsigned)(off & 0xffffffffull), (int)(unsigned)(off >> 32));
@@ -991,7 +1014,10 @@ __global__ void big_cells_kernel(CellBuffers P) {
     item = __shfl_sync(FULL, item, 0);
     if (item >= total) break;
     const int si = P.ovf_list[item];
-    if (!big_build_cell(P, A, si, ct, empties)) {
+    const long long amb0 = ct.fp64amb;
+    const bool built = big_build_cell(P, A, si, ct, empties);
+    if (__any_sync(FULL, ct.fp64amb != amb0) && lane == 0) record_ambiguous(P.st, P.amb_list, P.amb_cap, P.perm[si]);
+    if (!built) {
       failed++;
       if (lane == 0) {
         const int orig = P.perm[si];

@@ -41,6 +41,8 @@ struct WarpSmem {
   int qref[32 * QPL];
   int qocc[32 * QPL];
   float rtab[64];          // cell radius per occupied-octant mask
+  int knn[kKnn];           // KNN warm start: the cell's nearest sites (sorted indices, -1 = none)
+  unsigned amb_mark;       // FP64-ambiguous sign count before the current cell
   int anchor[PCAP];        // FP64 integration: one vertex per face
   double vd64[3 * 32 * VPL];  // FP64 integration: vertex positions
   WarpCounters ct;

@@ -23,6 +23,8 @@ constexpr int kMaxSites = 1 << 26;      // leaf refs pack the first site in 26 b
 constexpr int kMaxSets = 1024;
 constexpr int kBigWarpsPerBlock = 8;  // large-cell path: one block of this many warps per SM
 constexpr uint32_t kEmptyTri = 0xffffffffu;
+constexpr int kKnn = 8;               // sites of the KNN warm start (App. A.6)
+constexpr int kKnnLeaf = -1;          // traversal reference of a cell's KNN list (no real leaf has it)
 
 // Leaf references: bit 31 set, bits 26..30 = count-1, bits 0..25 = first.
 __host__ __device__ inline int make_leaf_ref(int first, int count) {
@@ -53,7 +55,24 @@ struct DevStatus {
   long long refined_volumes;
   long long ovf_reason[4];  // queue, vertices, planes, neighbours
   long long btape_used;     // bytes of the large-cell tape in use
+  // counters of the large-cell pass (the fields above count the main pass)
+  long long large_candidates;
+  long long large_clips;
+  long long large_nodes;
+  long long large_vtests;
+  long long large_newv;
+  long long btape_records;   // large-cell polytopes written to the large-cell tape
+  long long btape_restored;  // ... restored from it by the last adjoint
+  int amb_count;             // cells with an FP64 sign test left inside its bound
+  int amb_pad;
 };
+
+// Record cell `orig` (original index) as one whose construction took an FP64
+// sign that was still inside its error bound.
+__device__ inline void record_ambiguous(DevStatus* st, int* list, int cap, int orig) {
+  const int k = atomicAdd(&st->amb_count, 1);
+  if (k < cap) list[k] = orig;
+}
 
 __device__ inline void set_error(DevStatus* st, int code) { atomicCAS(&st->error, 0, code); }
 
@@ -268,6 +287,11 @@ struct CellBuffers {
   vd_config cfg;
   char* btape;           // large-cell tape (polytopes of cells past the register path), or nullptr
   long long btape_cap;   // its bytes
+  int* amb_list;         // [amb_cap] original ids of cells with an FP64-ambiguous sign test
+  int amb_cap;
+  int cell_begin;        // the cells this build makes: sorted indices [cell_begin, cell_end)
+  int cell_end;          //   (all of [0, n) unless the context is partitioned)
+  const int* knn;        // [n * kKnn] nearest sites (sorted indices, -1 = none) for warm_start = 2
 };
 
 constexpr int kSortThreads = 512;
@@ -308,6 +332,7 @@ cudaError_t launch_build_bvh(const uint64_t* keys, const float4* sites, int n, i
                              SetInfo* sets, int nsets, DevStatus* st, cudaStream_t s);
 cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, const std::function<void()>& between);
 cudaError_t launch_cells_thread(const CellBuffers& c, int num_sms, cudaStream_t s);
+cudaError_t launch_knn(const CellBuffers& c, int* knn, cudaStream_t s);
 cudaError_t launch_csr(const CellBuffers& c, int32_t* offsets, int32_t* neighbors, int64_t cap, int64_t* nnz_out,
                        long long* block_sums, int32_t* user_status, bool recount, cudaStream_t s);
 cudaError_t launch_backward(const BackBuffers& b, int num_sms, cudaStream_t s);

@@ -15,6 +15,8 @@
 // register-resident clipping. Cells that outgrow the register capacity, or
 // have more than VD_NOALLOC_ROW neighbours, are reported in the status word
 // instead of moving to the large-cell path (which needs an arena).
+#include <cuda.h>  // CUcontext / CUresult types of the two driver calls looked up below
+
 #include <mutex>
 
 #include "vd_clip.cuh"
@@ -61,6 +63,18 @@ __global__ void na_pack_kernel(const float* __restrict__ xyz, const float* __res
     }
     S->loser[i] = lose ? 1 : 0;
   }
+}
+
+// A cell this entry point cannot hold (register capacity, or more than
+// kNaRow neighbours): count -1, NaN volume and centroid, status word set.
+__device__ inline void overflow_row(int i, int32_t* counts, float* vol, float* cen, NoAllocScratch* SC) {
+  const float qnan = __int_as_float(0x7fc00000);
+  counts[i] = -1;
+  vol[i] = qnan;
+  cen[3 * (size_t)i] = qnan;
+  cen[3 * (size_t)i + 1] = qnan;
+  cen[3 * (size_t)i + 2] = qnan;
+  atomicCAS(&SC->error, 0, VD_ERR_CELL_OVERFLOW);
 }
 
 // One warp per cell, every other site a candidate.
@@ -136,11 +150,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t*
       }
     }
     if (overflow) {
-      if (lane == 0) {
-        counts[i] = -1;
-        vol[i] = __int_as_float(0x7fc00000);
-        atomicCAS(&SC->error, 0, VD_ERR_CELL_OVERFLOW);
-      }
+      if (lane == 0) overflow_row(i, counts, vol, cen, SC);
       continue;
     }
     if (empty) {
@@ -168,11 +178,7 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t*
     }
     __syncwarp();
     if (nvals > kNaRow) {
-      if (lane == 0) {
-        counts[i] = -1;
-        vol[i] = __int_as_float(0x7fc00000);
-        atomicCAS(&SC->error, 0, VD_ERR_CELL_OVERFLOW);
-      }
+      if (lane == 0) overflow_row(i, counts, vol, cen, SC);
       continue;
     }
     int32_t* row = nbrs + (size_t)i * kNaRow;
@@ -247,21 +253,58 @@ __global__ void __launch_bounds__(32 * kNaWarps) na_cells_kernel(int n, int32_t*
 
 __global__ void na_status_kernel(const NoAllocScratch* S, int32_t* status) { *status = S->error; }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array on the current device. It is looked
+// up once per device and CUDA context (with that device current) and cached;
+// a cudaDeviceReset gives the device a new context (and the module a new
+// copy of the array), so the cache is keyed by the context's id, read through
+// two driver calls that the runtime hands out (no link to the driver
+// library). If that id cannot be read, the address is looked up on every
+// call, which allocates nothing either.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
 std::mutex g_mu;
-void* g_addr[64] = {};
+struct ScratchSlot {
+  void* addr;
+  unsigned long long ctx_id;
+};
+ScratchSlot g_slot[64] = {};
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+bool g_entry_tried = false;
+
+bool context_id(unsigned long long* id) {
+  if (!g_entry_tried) {
+    g_entry_tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_get_id = reinterpret_cast<CtxGetIdFn>(f);
+  }
+  CUcontext c = nullptr;
+  if (!g_get_current || !g_get_id || g_get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return g_get_id(c, id) == CUDA_SUCCESS;
+}
 
 int scratch_on_device(NoAllocScratch** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VD_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  unsigned long long id = 0;
+  const bool have_id = context_id(&id);
+  ScratchSlot& S = g_slot[dev];
+  if (!S.addr || !have_id || S.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return VD_ERR_CUDA;
-    g_addr[dev] = p;
+    S.addr = p;
+    S.ctx_id = have_id ? id : 0;
   }
-  *out = static_cast<NoAllocScratch*>(g_addr[dev]);
+  *out = static_cast<NoAllocScratch*>(S.addr);
   return VD_OK;
 }
 
@@ -284,13 +327,27 @@ extern "C" int vd_cells_noalloc(const float* sites_xyz, const float* weights, in
   // the work counter and the error word must start at zero on every call
   if (cudaMemsetAsync(&S->work, 0, 2 * sizeof(int), s) != cudaSuccess) return VD_ERR_CUDA;
   int nn = (int)n;
-  na_pack_kernel<<<(nn + 255) / 256, 256, 0, s>>>(sites_xyz, weights, nn, bbox, S);
   int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess)
+    return VD_ERR_CUDA;
   int blocks = (nn + kNaWarps - 1) / kNaWarps;
   if (sms > 0 && blocks > 4 * sms) blocks = 4 * sms;
-  na_cells_kernel<<<blocks, 32 * kNaWarps, 0, s>>>(nn, counts, neighbors, volume, centroid, S);
-  na_status_kernel<<<1, 1, 0, s>>>(S, status);
-  return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+  // each launch through cudaLaunchKernel, whose return value is that
+  // launch's own status: an error left by the caller's earlier work is
+  // neither reported as ours nor cleared
+  const float* w = weights;
+  void* pack_args[] = {(void*)&sites_xyz, (void*)&w, (void*)&nn, (void*)&bbox, (void*)&S};
+  if (cudaLaunchKernel((const void*)na_pack_kernel, dim3((nn + 255) / 256), dim3(256), pack_args, 0, s) !=
+      cudaSuccess)
+    return VD_ERR_CUDA;
+  void* cell_args[] = {(void*)&nn, (void*)&counts, (void*)&neighbors, (void*)&volume, (void*)&centroid, (void*)&S};
+  if (cudaLaunchKernel((const void*)na_cells_kernel, dim3(blocks), dim3(32 * kNaWarps), cell_args, 0, s) !=
+      cudaSuccess)
+    return VD_ERR_CUDA;
+  const NoAllocScratch* Sc = S;
+  void* st_args[] = {(void*)&Sc, (void*)&status};
+  if (cudaLaunchKernel((const void*)na_status_kernel, dim3(1), dim3(1), st_args, 0, s) != cudaSuccess)
+    return VD_ERR_CUDA;
+  return VD_OK;
 }

@@ -510,12 +510,15 @@ __global__ void __launch_bounds__(128) cells_thread_kernel(CellBuffers P) {
   while (true) {
     int base = 0;
     if (lane == 0) base = atomicAdd(&P.work[0], 32);
-    base = __shfl_sync(FULL, base, 0);
-    if (base >= P.n) break;
+    base = __shfl_sync(FULL, base, 0) + P.cell_begin;
+    if (base >= P.cell_end) break;
     const int si = base + (int)lane;
-    if (si < P.n) {
+    if (si < P.cell_end) {
       int reason = 0;
-      if (!t_build_cell(P, si, ct, empties, reason)) {
+      const long long amb0 = ct.fp64amb;
+      const bool built = t_build_cell(P, si, ct, empties, reason);
+      if (ct.fp64amb != amb0) record_ambiguous(P.st, P.amb_list, P.amb_cap, P.perm[si]);
+      if (!built) {
         overflows++;
         reasons[reason]++;
         const int orig = P.perm[si];

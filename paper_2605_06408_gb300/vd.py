@@ -29,7 +29,7 @@ ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
     "vd_build", "vd_copy_neighbors", "vd_build_batched", "vd_backward", "vd_get_timings", "vd_get_status",
     "vd_error_string", "vd_cells_noalloc", "vd_autotune", "vd_autotune_batched", "vd_cells_mesh",
-    "vd_backward_mesh",
+    "vd_backward_mesh", "vd_ambiguous_cells", "vd_set_partition",
 )
 VD_TUNE_FORCE = 1
 
@@ -91,7 +91,11 @@ class VdStatus(ctypes.Structure):
         for k in ("nnz", "empty_cells", "overflow_cells", "failed_cells", "fp64_fallbacks", "fp64_ambiguous",
                   "candidates", "clips", "nodes", "vertex_tests", "new_vertices", "refined_vertices",
                   "refined_volumes")
-    ] + [("overflow_reason", ctypes.c_int64 * 4)]
+    ] + [("overflow_reason", ctypes.c_int64 * 4)] + [
+        (k, ctypes.c_int64)
+        for k in ("large_candidates", "large_clips", "large_nodes", "large_vertex_tests", "large_new_vertices",
+                  "large_tape_records", "large_tape_restored", "ambiguous_cells")
+    ]
 
 
 _lock = threading.Lock()
@@ -134,6 +138,8 @@ def load_library(build_if_missing: bool = True):
         lib.vd_backward_mesh.argtypes = [P, P, P, P, P, P, P, P]
         lib.vd_autotune_batched.argtypes = [P, P, P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(VdConfig), P]
+        lib.vd_ambiguous_cells.argtypes = [P, P, I64, P]
+        lib.vd_set_partition.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.vd_error_string.argtypes = [I]
         lib.vd_error_string.restype = ctypes.c_char_p
         for f in ABI_FUNCTIONS:
@@ -269,6 +275,12 @@ class Context:
         _check(rc, "vd_autotune_batched")
         self.config = {k: getattr(best, k) for k, _ in VdConfig._fields_}
         return dict(self.config)
+
+    def set_partition(self, part: int, nparts: int):
+        """Build only part `part` of `nparts` contiguous Morton-order ranges
+        of the cells from now on (vd_set_partition); (0, 1) builds all."""
+        _check(self._lib.vd_set_partition(self._h, int(part), int(nparts)), "vd_set_partition")
+        self.partition = (int(part), int(nparts))
 
     def reserve(self, n: int, weighted: bool = False):
         _check(self._lib.vd_reserve(self._h, int(n), int(weighted)), "vd_reserve")
@@ -417,6 +429,19 @@ class Context:
         t = VdTimings()
         _check(self._lib.vd_get_timings(self._h, ctypes.byref(t)), "vd_get_timings")
         return {k: getattr(t, k) for k, _ in VdTimings._fields_ if k != "reserved"}
+
+    def ambiguous_cells(self):
+        """Original indices (int64 numpy array, sorted, unique) of the cells
+        of the last forward build that took an FP64 sign test still inside
+        its FP64 error bound (vd_ambiguous_cells)."""
+        import numpy as np
+
+        cnt = ctypes.c_int64()
+        _check(self._lib.vd_ambiguous_cells(self._h, None, 0, ctypes.byref(cnt)), "vd_ambiguous_cells")
+        buf = np.zeros(max(int(cnt.value), 1), np.int64)
+        _check(self._lib.vd_ambiguous_cells(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.shape[0],
+                                            ctypes.byref(cnt)), "vd_ambiguous_cells")
+        return np.unique(buf[:min(int(cnt.value), buf.shape[0])])
 
     def status(self) -> dict:
         st = VdStatus()

@@ -83,13 +83,15 @@ def test_vertex_gradient_matches_oracle(vdmod, weighted):
     gp = gp.cpu().numpy().astype(np.float64)
     touched = np.abs(gpo).max(1) > 0
     err = np.abs(gp - gpo).max(1)[touched] / np.abs(gpo).max(1)[touched]
-    assert np.quantile(err, 0.99) < 1e-3 and err.max() < 2e-2, (np.quantile(err, 0.99), err.max())
+    # about 10x the measured errors (Voronoi: max 4.4e-6, p99 2.4e-6; power:
+    # max 1.1e-5, p99 2.6e-6; power weights: p99 2.0e-6)
+    assert np.quantile(err, 0.99) < 3e-5 and err.max() < 1.2e-4, (np.quantile(err, 0.99), err.max())
     assert np.abs(gp[~touched]).max() == 0.0
     if weighted:
         gw = gw.cpu().numpy().astype(np.float64)
         tw = np.abs(gwo) > 0
         ew = np.abs(gw - gwo)[tw] / np.maximum(np.abs(gwo)[tw], 1e-3 * np.abs(gwo).max())
-        assert np.quantile(ew, 0.99) < 1e-3
+        assert np.quantile(ew, 0.99) < 3e-5 and ew.max() < 1.2e-4, (np.quantile(ew, 0.99), ew.max())
 
 
 def test_mesh_autograd_function(vdmod):

@@ -99,21 +99,34 @@ def test_workloads_100k_full(ctx, kind):
         w = W.gaussian_weights(x, 16)
     res = build(ctx, x, w)
     ref = oracle.cells(x, w, max_nbrs=8192)
-    assert ref["stats"]["ambiguous"] == 0
+    assert ref["stats"]["ambiguous"] == 0 and ref["stats"]["degenerate"] == 0
     assert_parity(res, ref, what=kind)
     st = ctx.status()
     assert st["error"] == 0 and st["fp64_ambiguous"] == 0
 
 
 def test_configs_at_full_size_sampled(ctx):
-    """1M mixture (Voronoi and power) at full size; 3000 sampled cells."""
+    """1M mixture (Voronoi and power) at full size: 3000 sampled cells, and
+    every cell whose build took an FP64 sign still inside its FP64 error
+    bound, against the oracle (whose every sign is exact)."""
     x = W.mixture(1_000_000, 1)
     rng = W.rng_for(99)
     sample = np.sort(rng.choice(len(x), 3000, replace=False))
+    sess = oracle.Session(x, None)
     for w in (None, W.power_weights(x, 2)):
+        if w is not None:
+            sess = oracle.Session(x, w)
         res = build(ctx, x, w)
-        ref = oracle.cells(x, w, cells=sample, max_nbrs=8192)
-        assert_parity(res, ref, cells=sample, what="1M" + (" power" if w is not None else ""))
+        what = "1M" + (" power" if w is not None else "")
+        ref = sess.cells(sample)
+        assert ref["stats"]["ambiguous"] == 0 and ref["stats"]["degenerate"] == 0
+        assert_parity(res, ref, cells=sample, what=what)
+        flagged = ctx.ambiguous_cells()
+        assert len(flagged) <= ctx.status()["ambiguous_cells"]
+        if len(flagged):
+            rf = sess.cells(flagged)
+            assert rf["stats"]["ambiguous"] == 0 and rf["stats"]["degenerate"] == 0
+            assert_parity(res, rf, cells=flagged, what=what + " FP64-ambiguous cells")
         # properties that hold at any size: volumes partition the box,
         # adjacency is symmetric
         vol = res.volume.double().sum().item()
@@ -127,22 +140,38 @@ def test_configs_at_full_size_sampled(ctx):
 
 # ------------------------------------------------------------------ knobs
 
-@pytest.mark.parametrize("cfg", [
-    {"cull_mode": 2}, {"cull_mode": 1}, {"traversal": 1}, {"leaf_size": 1}, {"leaf_size": 32},
-    {"verts_per_lane": 4, "queue_per_lane": 1}, {"verts_per_lane": 2, "queue_per_lane": 1},
-    {"warps_per_block": 8, "blocks_per_sm": 2}, {"warm_start": 1},
-    {"cell_mode": 1}, {"cell_mode": 1, "cull_mode": 1}, {"cell_mode": 1, "traversal": 1},
-    {"cell_mode": 1, "leaf_size": 8},
-])
-def test_configuration_knobs_give_identical_cells(vdmod, cfg):
+@pytest.fixture(scope="module")
+def knob_inputs():
+    """A clustered Voronoi set and a power set with empty cells, with the
+    oracle's cells of both."""
     x = W.mixture(6000, 21)
-    w = W.power_weights(x, 22)
-    base = vdmod.Context(0)
-    other = vdmod.Context(0, cfg)
-    a = build(base, x, w)
-    b = build(other, x, w)
-    assert torch.equal(a.offsets, b.offsets) and torch.equal(a.neighbors, b.neighbors)
-    assert torch.allclose(a.volume, b.volume, rtol=1e-5, atol=0)
+    out = {}
+    for name, w in (("voronoi", None), ("power", W.power_weights(x, 22))):
+        ref = oracle.cells(x, w, max_nbrs=8192)
+        assert ref["stats"]["ambiguous"] == 0 and ref["stats"]["degenerate"] == 0
+        out[name] = (w, ref)
+    assert np.count_nonzero(out["power"][1]["vol"] == 0) > 100
+    return x, out
+
+
+@pytest.mark.parametrize("cfg", [
+    {}, {"cull_mode": 2}, {"cull_mode": 1}, {"traversal": 1}, {"leaf_size": 1}, {"leaf_size": 32},
+    {"verts_per_lane": 4, "queue_per_lane": 1}, {"verts_per_lane": 2, "queue_per_lane": 1},
+    {"warps_per_block": 8, "blocks_per_sm": 2}, {"warm_start": 1}, {"warm_start": 1, "verts_per_lane": 4},
+    {"cell_mode": 1}, {"cell_mode": 1, "cull_mode": 1}, {"cell_mode": 1, "traversal": 1},
+    {"cell_mode": 1, "leaf_size": 8}, {"cull_mode": 1, "traversal": 1},
+])
+def test_configuration_knobs_match_oracle(vdmod, knob_inputs, cfg):
+    """Every knob (warm start, the ablations of Sec. 5: isotropic culling,
+    no culling, depth-first traversal; capacities, block shapes, the thread
+    form) builds the oracle's cells, Voronoi and power (with empty cells)."""
+    x, refs = knob_inputs
+    ctx = vdmod.Context(0, cfg)
+    for name, (w, ref) in refs.items():
+        res = build(ctx, x, w)
+        assert_parity(res, ref, what=f"{name} {cfg}")
+        st = ctx.status()
+        assert st["error"] == 0 and st["failed_cells"] == 0
 
 
 # ------------------------------------------------------------------ edge cases
@@ -247,15 +276,19 @@ def test_backward_matches_oracle_gradient(ctx, weighted):
     ogp, ogw, _ = oracle.grad(x, w, W.UNIT_BOX, c, d)
     gp = gp.cpu().numpy().astype(np.float64)
     # FP32 adjoint vs FP64 analytic gradient: per-site error relative to the
-    # site's own gradient scale (terms scale like 1/V for the centroid part)
+    # site's own gradient scale (terms scale like 1/V for the centroid part).
+    # Bounds are about 10x the measured errors (Voronoi: max 1.3e-5, p99
+    # 2.0e-6; power: max 8.3e-4 on a sliver cell of volume ~1e-12, p99 4.3e-6;
+    # power weights: max 5.9e-4, p99 1.2e-5)
     scale = np.maximum(np.abs(ogp).max(1), 1e-3 * np.abs(ogp).max())
     err = np.abs(gp - ogp).max(1) / scale
-    assert np.quantile(err, 0.99) < 1e-3 and err.max() < 5e-2, (np.quantile(err, 0.99), err.max())
+    emax, ep99 = (8e-3, 4e-5) if weighted else (1.3e-4, 2e-5)
+    assert np.quantile(err, 0.99) < ep99 and err.max() < emax, (np.quantile(err, 0.99), err.max())
     if weighted:
         gw = gw.cpu().numpy().astype(np.float64)
         sw = np.maximum(np.abs(ogw), 1e-3 * np.abs(ogw).max())
         ew = np.abs(gw - ogw) / sw
-        assert np.quantile(ew, 0.99) < 1e-3 and ew.max() < 5e-2
+        assert np.quantile(ew, 0.99) < 1.2e-4 and ew.max() < 6e-3, (np.quantile(ew, 0.99), ew.max())
 
 
 def test_autograd_function(vdmod):
@@ -284,7 +317,12 @@ def test_backward_tape_equals_recompute(vdmod, weighted):
     ctx = vdmod.Context(0, {"tape": 1})
     res = build(ctx, x, w)
     gp_t, gw_t = ctx.backward(gv, gc, want_weights=weighted)
+    st = ctx.status()
+    # the large cells' polytopes came from the large-cell tape: every record
+    # the forward wrote was read back
+    assert st["large_tape_records"] > 0 and st["large_tape_restored"] == st["large_tape_records"]
     gp_r, gw_r = ctx.backward(gv, gc, want_weights=weighted, recompute=True)
+    assert ctx.status()["large_tape_restored"] == 0
     # both against the oracle on 150 cells and their neighbours
     off = res.offsets.cpu().numpy().astype(np.int64)
     nb = res.neighbors.cpu().numpy()
@@ -292,17 +330,24 @@ def test_backward_tape_equals_recompute(vdmod, weighted):
     K = K[np.diff(off)[K] > 0]
     cells = np.unique(np.concatenate([K] + [nb[off[q]:off[q + 1]] for q in K]))
     ogp, _, _ = oracle.grad(x, w, W.UNIT_BOX, c, d, cells=cells)
+    # bounds about 10x the measured errors against the oracle (Voronoi: max
+    # 2.2e-6, p99 1.6e-6; power: max 1.2e-4, p99 2.8e-5)
+    emax, ep99 = (1.2e-3, 3e-4) if weighted else (2.2e-5, 1.6e-5)
     for g in (gp_t, gp_r):
         gg = g.cpu().numpy()[K].astype(np.float64)
         err = np.abs(gg - ogp[K]).max(1) / np.maximum(np.abs(ogp[K]).max(1), 1e-30)
-        assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
-    # tape vs recompute on every site
+        assert np.quantile(err, 0.99) < ep99 and err.max() < emax, (np.quantile(err, 0.99), err.max())
+    # tape vs recompute on every site: FP32 rounding of the vertices, which
+    # sliver power cells amplify (measured: Voronoi max 1.1e-5, p999 3.3e-6;
+    # power max 1.4e-2 on one sliver cell, p999 6.2e-5; weights p99 1.0e-5)
     scale = gp_r.abs().max(dim=1).values.clamp_min(1e-30)
     rel = (gp_t - gp_r).abs().max(dim=1).values / scale
-    assert rel.quantile(0.999).item() < 1e-3 and rel.max().item() < 0.05
+    rmax, r999 = (0.05, 6e-4) if weighted else (1.1e-4, 3.3e-5)
+    assert rel.quantile(0.999).item() < r999 and rel.max().item() < rmax, (rel.quantile(0.999).item(),
+                                                                            rel.max().item())
     if weighted:
         sw = gw_r.abs().clamp_min(1e-3 * gw_r.abs().max().item())
-        assert ((gw_t - gw_r).abs() / sw).quantile(0.99).item() < 1e-3
+        assert ((gw_t - gw_r).abs() / sw).quantile(0.99).item() < 1e-4
     # a context without a tape re-clips: the same as recompute
     nt = vdmod.Context(0, {"tape": 0})
     build(nt, x, w)

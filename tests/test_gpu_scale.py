@@ -29,6 +29,8 @@ def dev(a):
 
 
 def check_rows(off, nb, vol, cen, ref, cells, base=0):
+    # every sign the oracle took is exact, and none is a true degeneracy
+    assert ref["stats"]["ambiguous"] == 0 and ref["stats"]["degenerate"] == 0
     for q, i in enumerate(cells):
         assert np.array_equal(nb[off[base + i]:off[base + i + 1]], ref["nbrs"][q]), (base, i)
     rv = ref["vol"]
@@ -54,6 +56,16 @@ def test_batched_256_sets_eager_and_graph(vdmod):
         cells = np.arange(b - a) if b - a <= 2000 else np.sort(W.rng_for(s).choice(b - a, 2000, replace=False))
         ref = oracle.cells(X[a:b], Wt[a:b] if flags[s] else None, W.UNIT_BOX, cells=cells)
         check_rows(off, nb, vol, cen, ref, cells, base=a)
+    # every cell whose build took an FP64 sign still inside its FP64 bound,
+    # against the oracle (exact signs), set by set
+    flagged = ctx.ambiguous_cells()
+    assert len(flagged) <= st["ambiguous_cells"] <= 65536
+    sets = np.searchsorted(offs, flagged, side="right") - 1
+    for s in np.unique(sets):
+        a, b = int(offs[s]), int(offs[s + 1])
+        cells = flagged[sets == s] - a
+        ref = oracle.cells(X[a:b], Wt[a:b] if flags[s] else None, W.UNIT_BOX, cells=cells)
+        check_rows(off, nb, vol, cen, ref, cells, base=a)
     # the same build captured once into a CUDA graph and replayed
     n = len(X)
     g_ctx = vdmod.Context(0)
@@ -77,7 +89,10 @@ def test_batched_256_sets_eager_and_graph(vdmod):
     assert torch.allclose(rg.volume, r.volume, rtol=1e-6, atol=0)
 
 
-def _grad_subset_check(x, w, res, gp, gw, c, d, k=200, seed=9):
+def _grad_subset_check(x, w, res, gp, gw, c, d, k=200, seed=9, emax=5e-4, ep99=1.2e-4):
+    """The adjoint on k sampled sites against the oracle's analytic gradient.
+    Default bounds are about 10x the errors measured on the 1M power diagram
+    (sites: max 4.8e-5, p99 1.2e-5; weights p99 3.2e-5)."""
     off = res.offsets.cpu().numpy().astype(np.int64)
     nb = res.neighbors.cpu().numpy()
     K = np.sort(W.rng_for(seed).choice(len(x), k, replace=False))
@@ -86,11 +101,11 @@ def _grad_subset_check(x, w, res, gp, gw, c, d, k=200, seed=9):
     ogp, ogw, _ = oracle.grad(x, w, W.UNIT_BOX, c, d, cells=cells)
     g = gp.cpu().numpy()[K].astype(np.float64)
     err = np.abs(g - ogp[K]).max(1) / np.maximum(np.abs(ogp[K]).max(1), 1e-30)
-    assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
+    assert np.quantile(err, 0.99) < ep99 and err.max() < emax, (np.quantile(err, 0.99), err.max())
     if gw is not None:
         gww = gw.cpu().numpy()[K].astype(np.float64)
         ew = np.abs(gww - ogw[K]) / np.maximum(np.abs(ogw[K]), 1e-3 * np.abs(ogw[K]).max())
-        assert np.quantile(ew, 0.99) < 1e-3
+        assert np.quantile(ew, 0.99) < 3e-4
 
 
 @pytest.mark.parametrize("weighted", [False, True])
@@ -102,7 +117,8 @@ def test_backward_at_1M(vdmod, weighted):
     res = ctx.build(dev(x), dev(w), W.UNIT_BOX)
     gp, gw = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=weighted)
     assert ctx.status()["error"] == 0
-    _grad_subset_check(x, w, res, gp, gw, c, d)
+    # measured: Voronoi max 3.5e-6, p99 9.8e-7; power max 4.8e-5, p99 1.2e-5
+    _grad_subset_check(x, w, res, gp, gw, c, d, emax=5e-4 if weighted else 3.5e-5, ep99=1.2e-4 if weighted else 1e-5)
 
 
 def test_surfaces_20M_forward_and_backward(vdmod):
@@ -114,13 +130,16 @@ def test_surfaces_20M_forward_and_backward(vdmod):
     off = res.offsets.cpu().numpy().astype(np.int64)
     nb = res.neighbors.cpu().numpy()
     samp = np.sort(W.rng_for(11).choice(len(x), 1500, replace=False))
+    flagged = ctx.ambiguous_cells()
+    samp = np.union1d(samp, flagged[:2000])  # with the cells that took an FP64-ambiguous sign
     ref = oracle.cells(x, None, W.UNIT_BOX, cells=samp)
     check_rows(off, nb, res.volume.cpu().numpy(), res.centroid.cpu().numpy(), ref, samp)
     # volumes partition the box at any size
     assert res.volume.double().sum().item() == pytest.approx(1.0, rel=1e-5)
     c, d = W.loss_coefficients(len(x), 4)
     gp, _ = ctx.backward(dev(c.astype(np.float32)), dev(d.astype(np.float32)), want_weights=False)
-    _grad_subset_check(x, None, res, gp, None, c, d, k=150, seed=12)
+    # measured: max 2.2e-6, p99 1.0e-6 (against the analytic gradient)
+    _grad_subset_check(x, None, res, gp, None, c, d, k=150, seed=12, emax=3e-5, ep99=1.2e-5)
     # FP64 central finite differences on 1,000 sites, combinatorics from the
     # oracle's own neighbour rows of those sites and their neighbours
     K = np.sort(W.rng_for(13).choice(len(x), 1000, replace=False))
@@ -137,7 +156,8 @@ def test_surfaces_20M_forward_and_backward(vdmod):
     fd, _ = oracle.fd_grad(x, None, W.UNIT_BOX, off, nb, c, d, K, hx=h)
     g = gp.cpu().numpy()[K].astype(np.float64)
     err = np.abs(g - fd).max(1) / np.maximum(np.abs(fd).max(1), 1e-30)
-    assert np.quantile(err, 0.99) < 1e-4 and err.max() < 1e-3, (np.quantile(err, 0.99), err.max())
+    # measured against FP64 central differences: max 2.2e-6, p99 1.1e-6
+    assert np.quantile(err, 0.99) < 1.2e-5 and err.max() < 3e-5, (np.quantile(err, 0.99), err.max())
 
 
 def test_bounded_helping_wait_reports_timeout(vdmod, monkeypatch):

@@ -28,11 +28,27 @@ def dev(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def same_cells(a, b):
-    assert torch.equal(a.offsets, b.offsets)
-    assert torch.equal(a.neighbors, b.neighbors)
-    assert torch.allclose(a.volume, b.volume, rtol=1e-5, atol=0)
-    assert torch.allclose(a.centroid, b.centroid, rtol=1e-5, atol=1e-7)
+def oracle_rows(res, x, w, box, cells, base=0):
+    """Rows base + cells of a build against the FP64 oracle's cells of the
+    set x: identical neighbour lists, volume and centroid within 1e-5."""
+    ref = oracle.cells(x, w, box, cells=cells, max_nbrs=8192)
+    assert ref["stats"]["ambiguous"] == 0 and ref["stats"]["degenerate"] == 0
+    off = res.offsets.cpu().numpy().astype(np.int64)
+    nb = res.neighbors.cpu().numpy()
+    for q, i in enumerate(cells):
+        assert np.array_equal(nb[off[base + i]:off[base + i + 1]], ref["nbrs"][q]), (base, i)
+    vol = res.volume.cpu().numpy().astype(np.float64)[base + cells]
+    assert np.all(np.abs(vol - ref["vol"]) <= 1e-5 * ref["vol"] + 1e-30)
+    cen = res.centroid.cpu().numpy().astype(np.float64)[base + cells]
+    assert np.all(np.linalg.norm(cen - ref["cen"], axis=1) <= 1e-5 * np.linalg.norm(ref["cen"], axis=1))
+
+
+def batched_against_oracle(res, X, Wt, offs, flags, sets, per_set=1500):
+    for s in sets:
+        a, b = int(offs[s]), int(offs[s + 1])
+        m = b - a
+        cells = np.arange(m) if m <= per_set else np.sort(W.rng_for(100 + s).choice(m, per_set, replace=False))
+        oracle_rows(res, X[a:b], Wt[a:b] if flags[s] else None, W.UNIT_BOX, cells, base=a)
 
 
 @pytest.mark.parametrize("kind", ["uniform", "power"])
@@ -57,21 +73,19 @@ def test_thread_form_matches_oracle(vdmod, kind):
     assert np.all(np.linalg.norm(cen - ref["cen"], axis=1) <= 1e-5 * np.linalg.norm(ref["cen"], axis=1))
 
 
-def test_thread_form_batched_equals_warp_form(vdmod):
+def test_thread_form_batched_matches_oracle(vdmod):
     X, Wt, offs, flags = W.batched(3)
     k = 24  # the first 24 sets (sizes 1e3..2e5, both kinds)
     n = int(offs[k])
     boxes = [W.UNIT_BOX] * k
-    a = vdmod.Context(0).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
     b = vdmod.Context(0, {"cell_mode": 1}).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
-    same_cells(a, b)
+    batched_against_oracle(b, X, Wt, offs, flags, range(0, k, 3))
 
 
 def test_autotune_single_set(vdmod):
     x = W.mixture(200_000, 41)
     w = W.power_weights(x, 42)
     xs, ws = dev(x), dev(w)
-    ref = vdmod.Context(0).build(xs, ws, W.UNIT_BOX)
     ctx = vdmod.Context(0)
     cfg = ctx.autotune(xs, ws, W.UNIT_BOX, max_trials=10)
     assert cfg["cell_mode"] in (0, 1) and cfg["verts_per_lane"] in (2, 4)
@@ -79,7 +93,8 @@ def test_autotune_single_set(vdmod):
     # no forward state after tuning
     with pytest.raises(vdmod.VdError):
         ctx.backward(torch.ones(len(x), device="cuda"), None)
-    same_cells(ctx.build(xs, ws, W.UNIT_BOX), ref)
+    cells = np.sort(W.rng_for(43).choice(len(x), 3000, replace=False))
+    oracle_rows(ctx.build(xs, ws, W.UNIT_BOX), x, w, W.UNIT_BOX, cells)
     # cached: the same key returns at once with the same configuration
     t0 = time.perf_counter()
     again = ctx.autotune(xs, ws, W.UNIT_BOX)
@@ -95,11 +110,11 @@ def test_autotune_batched(vdmod):
     k = 16
     n = int(offs[k])
     boxes = [W.UNIT_BOX] * k
-    ref = vdmod.Context(0).build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
     ctx = vdmod.Context(0)
     cfg = ctx.autotune_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k], max_trials=6)
     assert cfg["cell_mode"] in (0, 1)
-    same_cells(ctx.build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k]), ref)
+    r = ctx.build_batched(dev(X[:n]), dev(Wt[:n]), offs[:k + 1], boxes, flags[:k])
+    batched_against_oracle(r, X, Wt, offs, flags, range(0, k, 2))
 
 
 @pytest.mark.parametrize("cell_mode", [0, 1])
@@ -118,6 +133,8 @@ def test_batched_adjoint_with_tape(vdmod, cell_mode):
     gp_r, gw_r = ctx.backward(gv, gc, want_weights=True, recompute=True)
     scale = gp_r.abs().max(dim=1).values.clamp_min(1e-30)
     rel = (gp_t - gp_r).abs().max(dim=1).values / scale
-    assert rel.quantile(0.999).item() < 1e-3 and rel.max().item() < 0.05
+    # measured (warp form): max 2.9e-3 on a sliver power cell, p999 2.5e-5
+    assert rel.quantile(0.999).item() < 2.5e-4 and rel.max().item() < 0.03, (rel.quantile(0.999).item(),
+                                                                              rel.max().item())
     if cell_mode == 1:  # no tape: the same computation (up to the order of the atomic sums)
         assert torch.allclose(gp_t, gp_r, rtol=1e-5, atol=1e-6 * gp_r.abs().max().item())
