@@ -781,8 +781,8 @@ int vd_ambiguous_cells(vd_ctx* ctx, int64_t* cells, int64_t capacity, int64_t* c
 // ---------------------------------------------------------------- autotuner
 //
 // Coordinate descent over the kernel form and its capacities: starting from
-// the context's configuration, each knob in turn (cell form, polytope
-// capacity, queue depth, leaf size, block size, warm start) takes each of
+// the context's configuration, each knob in turn (cell form, warm start,
+// polytope capacity, queue depth, leaf size, block size) takes each of
 // its other values; a trial is one warm-up build then the faster of two
 // timed builds (CUDA events on the caller's stream) of the caller's input,
 // and a value is kept if it is at least 2% faster. A configuration under
@@ -867,10 +867,12 @@ static int autotune(vd_ctx* ctx, int64_t n, int nsets, int weighted, const std::
       int count;
       bool warp_only;
     };
+    // the warm start comes before the leaf size: the best leaf size depends
+    // on it (with the KNN start, larger leaves win on every workload here)
     const Knob knobs[] = {
-        {&vd_config::cell_mode, {0, 1, 0}, 2, false},  {&vd_config::verts_per_lane, {2, 4, 0}, 2, true},
-        {&vd_config::queue_per_lane, {2, 4, 8}, 3, true}, {&vd_config::leaf_size, {8, 16, 32}, 3, false},
-        {&vd_config::warps_per_block, {2, 4, 8}, 3, true}, {&vd_config::warm_start, {0, 1, 2}, 3, true},
+        {&vd_config::cell_mode, {0, 1, 0}, 2, false},     {&vd_config::warm_start, {0, 1, 2}, 3, true},
+        {&vd_config::verts_per_lane, {2, 4, 0}, 2, true}, {&vd_config::queue_per_lane, {2, 4, 8}, 3, true},
+        {&vd_config::leaf_size, {8, 16, 32}, 3, false},   {&vd_config::warps_per_block, {2, 4, 8}, 3, true},
     };
     for (const Knob& k : knobs) {
       if (k.warp_only && cur.cell_mode != 0) continue;

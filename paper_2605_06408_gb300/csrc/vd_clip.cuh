@@ -230,8 +230,11 @@ __device__ __forceinline__ bool node_test_r(float4 lo, float4 hi, float4 me, Rad
     return true;
   }
   float D2 = D * D;
-  lb = (D2 + c - kCullPad * (D2 + fabsf(me.w) + fabsf(lo.w))) / (2.0f * D);
-  key = (D2 + c) / (2.0f * D) - R;
+  // one approximate reciprocal for both quotients: its error (a few ulp)
+  // is far inside the relative pad of 1e-5 that keeps lb a lower bound
+  const float inv = __fdividef(0.5f, D);
+  lb = (D2 + c - kCullPad * (D2 + fabsf(me.w) + fabsf(lo.w))) * inv;
+  key = (D2 + c) * inv - R;
   if (cull_mode == 2) return true;
   return !(lb > R * (1.0f + kCullPad));
 }

@@ -23,7 +23,10 @@ constexpr int kMaxSites = 1 << 26;      // leaf refs pack the first site in 26 b
 constexpr int kMaxSets = 1024;
 constexpr int kBigWarpsPerBlock = 8;  // large-cell path: one block of this many warps per SM
 constexpr uint32_t kEmptyTri = 0xffffffffu;
-constexpr int kKnn = 8;               // sites of the KNN warm start (App. A.6)
+#ifndef VD_KNN
+#define VD_KNN 8
+#endif
+constexpr int kKnn = VD_KNN;          // sites of the KNN warm start (App. A.6)
 constexpr int kKnnLeaf = -1;          // traversal reference of a cell's KNN list (no real leaf has it)
 
 // Leaf references: bit 31 set, bits 26..30 = count-1, bits 0..25 = first.
