@@ -626,7 +626,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    def rate(t_ms):
+    def job_value(t_ms):
+        """Whole-job Mcells/s for a step of t_ms (the slowest rank's)."""
         return partition_rate(n, t_ms) if split else job_rate(n, ws, t_ms)
 
     props = torch.cuda.get_device_properties(dev)
@@ -659,7 +660,7 @@ def run_ours(args):
 
     out = {
         "metric": METRIC,
-        "value": rate(ms),
+        "value": job_value(ms),
         "unit": "Mcells/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -680,10 +681,10 @@ def run_ours(args):
                    "libvd": {k: v for k, v in ctx.config.items()},
                    "autotuned": not args.no_autotune, "autotune_s": tune_s,
                    "weight_ratio": args.weight_ratio if args.workload == "uniform1M_wratio" else None},
-        "fwd_bwd_mcells_s": None if fb_ms is None else rate(fb_ms),
+        "fwd_bwd_mcells_s": None if fb_ms is None else job_value(fb_ms),
         "fwd_bwd_config": "the timed configuration with tape = 1 (the forward keeps its cells for the adjoint)",
         "fwd_bwd_ms_per_step": fb_ms,
-        "e2e": {"value": rate(e2e_ms), "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(e2e_ms), "unit": "Mcells/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "clocks": clocks,

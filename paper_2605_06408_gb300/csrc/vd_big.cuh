@@ -401,6 +401,8 @@ __device__ __forceinline__ bool chunk_may_cut(const PlaneT<float>& H, float4 lo,
 
 // Polytopes of at most this many chunks are scanned without the box stage.
 constexpr int kBoxStage = 2;
+// Chunk ranges of at most this many chunks test their boxes one lane per plane.
+constexpr int kByPlaneChunks = 12;
 
 // Batch filter: which of the k <= 32 planes staged in A.hs / A.hse may
 // cut the polytope (some vertex outside or ambiguous)? Bit t of the result
@@ -442,13 +444,34 @@ __device__ __forceinline__ void for_staged_planes(const float4* hs, const float*
 // whose test reaches its box.
 __device__ inline uint32_t filter_chunks(const float4* vp, const float4* cb, int nv, int q0, int q1,
                                          const float4* hs, const float* hse, uint32_t open, bool boxes,
-                                         long long& tested) {
+                                         long long& tested, bool group = false) {
   const unsigned lane = lane_id();
   uint32_t cuts = 0;
+  // a helping group (a few chunks of another warp's polytope) tests its
+  // boxes with one lane per staged plane, so that all lanes work; a warp's
+  // own filter takes one lane per chunk and loops over the open planes
+  const bool by_plane = group && boxes && q1 - q0 <= kByPlaneChunks;
+  PlaneT<float> Hl;
+  Hl.nx = Hl.ny = Hl.nz = Hl.b = Hl.e = 0.0f;
+  if (by_plane && ((open >> lane) & 1u)) {
+    const float4 h = hs[lane];
+    Hl.nx = h.x;
+    Hl.ny = h.y;
+    Hl.nz = h.z;
+    Hl.b = h.w;
+    Hl.e = hse[lane];
+  }
   for (int cbase = q0; cbase < q1 && open; cbase += 32) {
     const int q = cbase + (int)lane;
     uint32_t fl = 0;
-    if (q < q1) {
+    if (by_plane) {
+      const int m = min(32, q1 - cbase);
+      for (int r = 0; r < m; r++) {
+        const float4 lo = cb[2 * (cbase + r)], hi = cb[2 * (cbase + r) + 1];
+        const uint32_t b = __ballot_sync(FULL, ((open >> lane) & 1u) && chunk_may_cut(Hl, lo, hi));
+        if ((int)lane == r) fl = b;
+      }
+    } else if (q < q1) {
       if (!boxes) {
         fl = open;
       } else {
@@ -568,7 +591,7 @@ __device__ inline int help_drain(HelpReq& r, int gen, long long& tested, int* st
     const float* hse = r.hse;
     const uint32_t open = (k >= 32 ? FULL : ((1u << k) - 1u)) & ~(uint32_t)vload((const int*)&r.cuts);
     const int q1 = min(nch, q0 + kHelpGroup);
-    const uint32_t cm = filter_chunks(vp, cb, nv, q0, q1, hs, hse, open, true, tested);
+    const uint32_t cm = filter_chunks(vp, cb, nv, q0, q1, hs, hse, open, true, tested, true);
     if (lane == 0) {
       if (cm) atomicOr(&r.cuts, cm);
       __threadfence_block();
@@ -791,15 +814,19 @@ static __device__ __noinline__ bool big_resolve64(const BigArena& A, uint64_t tr
   return s > 0.0;
 }
 
-// Clip by plane H of site hpid (App. B), memory-resident form.
+// Clip by plane H of site hpid (App. B), memory-resident form. `filtered`:
+// the batch filter found that the plane may cut this cell (a vertex outside
+// or ambiguous), so the read-only pass that screens candidates which cut
+// nothing is skipped; the classifying pass alone still returns CLIP_NONE
+// when earlier clips left nothing outside.
 static __device__ int big_clip(BigCell& c, const BigArena& A, const PlaneT<float>& H, int hpid,
-                        const float4* __restrict__ sites, Counters& ct, bool counters) {
+                        const float4* __restrict__ sites, Counters& ct, bool counters, bool filtered = false) {
   const unsigned lane = lane_id(), lt = lanemask_lt();
   if (c.npl >= kBigGc) big_gc(c, A);
   if (c.npl >= kBigP) return CLIP_OVERFLOW;
   // read-only first pass over the chunks whose box the plane reaches; most
   // candidates cut nothing and end here without writes
-  {
+  if (!filtered) {
     bool any = false;
     const int nch = (c.nv + 31) >> 5;
     long long tested = 0;

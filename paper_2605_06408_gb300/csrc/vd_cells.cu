@@ -575,7 +575,7 @@ __device__ int big_flush(BigCell& c, const BigArena& A, const float4* __restrict
     const int hj = A.hid[src];
     if ((int)lane == src) keep = false;
     km &= ~(1u << src);
-    const int rc = big_clip(c, A, Hb, hj, sites, ct, counters);
+    const int rc = big_clip(c, A, Hb, hj, sites, ct, counters, true);
     if (rc == CLIP_EMPTY || rc == CLIP_OVERFLOW) return rc;
     if (rc == CLIP_DONE) {
       c.dirty = true;

@@ -552,8 +552,18 @@ __device__ __forceinline__ void init_cell(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL,
       b = d;
       d = t;
     }
-    PlaneT<float> A = load_plane(S, a), B = load_plane(S, b), D = load_plane(S, d);
-    vertex3<float>(A, B, D, c.vx[0], c.vy[0], c.vz[0], c.ve[0]);
+    // box corner: the three axis-aligned planes meet at (+-b) exactly (the
+    // solve of vertex3 has determinant 1 and unit cofactors here), and its
+    // error bound reduces to the terms below (vertex3's bound with W = 1)
+    const float4 Px = S.pl[sx], Py = S.pl[2 + sy], Pz = S.pl[4 + sz];
+    const float u = Num<float>::u;
+    c.vx[0] = sx ? -Px.w : Px.w;
+    c.vy[0] = sy ? -Py.w : Py.w;
+    c.vz[0] = sz ? -Pz.w : Pz.w;
+    const float x1 = fabsf(c.vx[0]) + fabsf(c.vy[0]) + fabsf(c.vz[0]);
+    const float sumE = S.pe[sx] + S.pe[2 + sy] + S.pe[4 + sz];
+    const float ep = (1.75f * sumE + (5.25f * 8.0f * u + 9.0f * u) * x1 + 6.0f * u * x1) + u * x1;
+    c.ve[0] = x1 < 1e30f ? 1.1f * ep + (8.0f * u + 3.0f * u) * x1 : INFINITY;
     c.vt[0] = (uint32_t)a | ((uint32_t)b << 8) | ((uint32_t)d << 16);
   }
   c.nv = 8;

@@ -158,6 +158,8 @@ def knob_inputs():
     {}, {"cull_mode": 2}, {"cull_mode": 1}, {"traversal": 1}, {"leaf_size": 1}, {"leaf_size": 32},
     {"verts_per_lane": 4, "queue_per_lane": 1}, {"verts_per_lane": 2, "queue_per_lane": 1},
     {"warps_per_block": 8, "blocks_per_sm": 2}, {"warm_start": 1}, {"warm_start": 1, "verts_per_lane": 4},
+    {"warm_start": 2}, {"warm_start": 2, "leaf_size": 8}, {"warm_start": 2, "traversal": 1},
+    {"warm_start": 2, "cull_mode": 1},
     {"cell_mode": 1}, {"cell_mode": 1, "cull_mode": 1}, {"cell_mode": 1, "traversal": 1},
     {"cell_mode": 1, "leaf_size": 8}, {"cull_mode": 1, "traversal": 1},
 ])
