@@ -25,13 +25,28 @@
 
 namespace vd {
 
+// GEN: the generic instantiation, which reads the ablation modes (culling,
+// traversal), the event counters and the precision mode from the
+// configuration; the default one (GEN = false) has them folded to
+// directional culling, best-first order, no counters and mixed precision, so
+// that code a timed build never runs stays out of its instruction stream
+// (measured on one GB300: 7-8% faster than one kernel for both).
+template <bool GEN>
+struct Knobs {
+  int cull, trav;
+  bool counters;
+  __device__ __forceinline__ explicit Knobs(const vd_config& g)
+      : cull(GEN ? g.cull_mode : 0), trav(GEN ? g.traversal : 0), counters(GEN && g.counters != 0) {}
+};
+
 // Process the sites of one leaf: pre-cull all of them in parallel, then
 // clip with the survivors in ascending power distance d_ij (Eq. 2).
-template <int VPL, int PCAP, int QPL>
+template <int VPL, int PCAP, int QPL, bool GEN>
 __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S, int ref, int si, int orig_i,
                             const CellBuffers& P, int skip0, int skip1) {
   const unsigned lane = lane_id();
-  const bool counters = P.cfg.counters != 0;
+  const Knobs<GEN> K(P.cfg);
+  const bool counters = K.counters;
   int j;
   bool act;
   if (ref == kKnnLeaf) {  // the KNN warm start: the cell's nearest sites
@@ -60,7 +75,7 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
     dup = nx == 0.0f && ny == 0.0f && nz == 0.0f;
     if (!dup) {
       float beta = 0.5f * (nn + (c.me.w - q.w));
-      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, P.cfg.cull_mode);
+      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, K.cull);
       if (keep) {
         H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
         dkey = H.b;
@@ -269,16 +284,17 @@ static __device__ __noinline__ bool cell_outputs(WarpSmem<VPL, PCAP, QPL>& S, co
 }
 
 // Build one cell and write its outputs. Returns false on overflow.
-template <int VPL, int PCAP, int QPL>
+template <int VPL, int PCAP, int QPL, bool GEN>
 __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, int si, int* row, long long& empties,
                            int& reason) {
   using C = Cell<VPL, PCAP, QPL>;
   constexpr int NPW = C::NPW;
   const unsigned lane = lane_id(), lt = lanemask_lt();
-  const bool counters = P.cfg.counters != 0;
+  const Knobs<GEN> K(P.cfg);
+  const bool counters = K.counters;
   C c;
   c.me = P.sites[si];
-  c.fp64 = P.cfg.precision == 0;
+  c.fp64 = GEN ? P.cfg.precision == 0 : true;
   const int orig_i = P.perm[si];
   if (P.loser[si]) {  // an exact duplicate site owns this position
     if (lane == 0) {
@@ -294,7 +310,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
   c.box = SI.lo;
-  const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
+  const int cull = K.cull, trav = K.trav;
   init_cell(c, S, cull);
   bool empty = false, overflow = false;
 
@@ -321,7 +337,7 @@ __device__ bool build_cell(const CellBuffers& P, WarpSmem<VPL, PCAP, QPL>& S, in
   while (!empty) {
     if (have) {
       if (ref_is_leaf(cur)) {
-        int rc = process_leaf(c, S, cur, si, orig_i, P, warm ? 0 : skip0, warm ? 0 : skip1);
+        int rc = process_leaf<VPL, PCAP, QPL, GEN>(c, S, cur, si, orig_i, P, warm ? 0 : skip0, warm ? 0 : skip1);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -492,7 +508,7 @@ __device__ inline void flush_warp_counters(const CellBuffers& P, const WarpCount
 #else
 #define VD_CELLS_BOUNDS
 #endif
-template <int VPL, int PCAP, int QPL>
+template <int VPL, int PCAP, int QPL, bool GEN>
 __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<VPL, PCAP, QPL>* Sw = reinterpret_cast<WarpSmem<VPL, PCAP, QPL>*>(smem_raw);
@@ -513,7 +529,7 @@ __global__ void VD_CELLS_BOUNDS cells_kernel(CellBuffers P) {
     // the ambiguous-sign count before the cell, kept in shared memory (not
     // a register live across the whole build)
     if (lane == 0) S.amb_mark = S.ct.fp64amb;
-    const bool built = build_cell<VPL, PCAP, QPL>(P, S, si, row, empties, reason);
+    const bool built = build_cell<VPL, PCAP, QPL, GEN>(P, S, si, row, empties, reason);
     __syncwarp();
     if (lane == 0 && S.ct.fp64amb != S.amb_mark) record_ambiguous(P.st, P.amb_list, P.amb_cap, orig);
     if (!built) {
@@ -586,10 +602,12 @@ __device__ int big_flush(BigCell& c, const BigArena& A, const float4* __restrict
   return CLIP_NONE;
 }
 
+template <bool GEN>
 __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig_i, const CellBuffers& P,
                         Counters& ct, int skip0, int skip1) {
   const unsigned lane = lane_id();
-  const bool counters = P.cfg.counters != 0;
+  const Knobs<GEN> K(P.cfg);
+  const bool counters = K.counters;
   int first = leaf_first(ref), cnt = leaf_count(ref);
   int j = first + (int)lane;
   bool act = (int)lane < cnt && j != si && (j < skip0 || j >= skip1);
@@ -606,7 +624,7 @@ __device__ int big_leaf(BigCell& c, const BigArena& A, int ref, int si, int orig
     dup = nx == 0.0f && ny == 0.0f && nz == 0.0f;
     if (!dup) {
       float beta = 0.5f * (nn + (c.me.w - q.w));
-      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, P.cfg.cull_mode);
+      keep = candidate_test(nx, ny, nz, nn, beta, c.me.w, q.w, c.alo, c.ahi, c.sc, c.srad, K.cull);
       if (keep) {
         H = site_plane<float>(c.me.x, c.me.y, c.me.z, c.me.w, q.x, q.y, q.z, q.w);
         dkey = H.b;
@@ -775,12 +793,14 @@ __device__ inline void big_tape_write(const BigCell& c, const BigArena& A, const
   __syncwarp();
 }
 
+template <bool GEN>
 __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, Counters& ct, long long& empties) {
   const unsigned lane = lane_id(), lt = lanemask_lt();
-  const bool counters = P.cfg.counters != 0;
+  const Knobs<GEN> K(P.cfg);
+  const bool counters = K.counters;
   BigCell c;
   c.me = P.sites[si];
-  c.fp64 = P.cfg.precision == 0;
+  c.fp64 = GEN ? P.cfg.precision == 0 : true;
   const int orig_i = P.perm[si];
   const int set = P.nsets > 1 ? (int)(P.keys[si] >> P.set_shift) : 0;
   const SetInfo& SI = P.sets[set];
@@ -789,7 +809,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     c.lo[k] = SI.lo[k];
     c.hi[k] = SI.hi[k];
   }
-  const int cull = P.cfg.cull_mode, trav = P.cfg.traversal;
+  const int cull = K.cull, trav = K.trav;
   big_init(c, A, cull);
   bool empty = false, overflow = false;
   int skip0 = 0, skip1 = 0;
@@ -797,7 +817,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
     const int lo = SI.first, hi = SI.first + SI.count;
     skip0 = max(lo, min(si - 16, hi - 32));
     skip1 = min(hi, skip0 + 32);
-    int rc = big_leaf(c, A, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, ct, 0, 0);
+    int rc = big_leaf<GEN>(c, A, make_leaf_ref(skip0, skip1 - skip0), si, orig_i, P, ct, 0, 0);
     if (rc == CLIP_NONE) rc = big_flush(c, A, P.sites, ct, counters);
     if (rc == CLIP_EMPTY) empty = true;
     if (rc == CLIP_OVERFLOW) return false;
@@ -811,7 +831,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
   while (!empty) {
     if (have) {
       if (ref_is_leaf(cur)) {
-        int rc = big_leaf(c, A, cur, si, orig_i, P, ct, skip0, skip1);
+        int rc = big_leaf<GEN>(c, A, cur, si, orig_i, P, ct, skip0, skip1);
         if (rc == CLIP_EMPTY) {
           empty = true;
           break;
@@ -991,6 +1011,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
   return true;
 }
 
+template <bool GEN>
 __global__ void big_cells_kernel(CellBuffers P) {
   const unsigned lane = lane_id();
   const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -1015,7 +1036,7 @@ __global__ void big_cells_kernel(CellBuffers P) {
     if (item >= total) break;
     const int si = P.ovf_list[item];
     const long long amb0 = ct.fp64amb;
-    const bool built = big_build_cell(P, A, si, ct, empties);
+    const bool built = big_build_cell<GEN>(P, A, si, ct, empties);
     if (__any_sync(FULL, ct.fp64amb != amb0) && lane == 0) record_ambiguous(P.st, P.amb_list, P.amb_cap, P.perm[si]);
     if (!built) {
       failed++;
@@ -1030,7 +1051,7 @@ __global__ void big_cells_kernel(CellBuffers P) {
   {
     long long tested = 0;
     big_help(A, tested);
-    if (P.cfg.counters) ct.vtests += tested;
+    if (GEN && P.cfg.counters) ct.vtests += tested;
   }
   flush_counters(P, ct, lane, empties, 0, failed);
 }
@@ -1039,7 +1060,8 @@ template <int VPL, int PCAP, int QPL>
 static cudaError_t launch_variant(const CellBuffers& c, int num_sms, cudaStream_t s) {
   int wpb = c.cfg.warps_per_block;
   size_t smem = sizeof(WarpSmem<VPL, PCAP, QPL>) * (size_t)wpb;
-  auto kern = cells_kernel<VPL, PCAP, QPL>;
+  const bool generic = c.cfg.cull_mode != 0 || c.cfg.traversal != 0 || c.cfg.counters != 0 || c.cfg.precision != 0;
+  auto kern = generic ? cells_kernel<VPL, PCAP, QPL, true> : cells_kernel<VPL, PCAP, QPL, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int per_sm = c.cfg.blocks_per_sm;
@@ -1074,9 +1096,12 @@ cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, cons
   between();
   // cells that overflowed the register-resident capacity
   const size_t big_smem = kBigSmemPerWarp * kBigWarpsPerBlock + sizeof(HelpBoard);
-  err = cudaFuncSetAttribute(big_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
+  const vd_config& gc = c.cfg;
+  auto big = (gc.cull_mode != 0 || gc.traversal != 0 || gc.counters != 0 || gc.precision != 0) ? big_cells_kernel<true>
+                                                                                                : big_cells_kernel<false>;
+  err = cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
   if (err != cudaSuccess) return err;
-  big_cells_kernel<<<num_sms, 32 * kBigWarpsPerBlock, big_smem, s>>>(c);
+  big<<<num_sms, 32 * kBigWarpsPerBlock, big_smem, s>>>(c);
   return cudaGetLastError();
 }
 
