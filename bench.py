@@ -317,7 +317,7 @@ def kernel_source_hash() -> str:
     import hashlib
 
     hsh = hashlib.sha256()
-    for f in ("vd_cells.cu", "vd_clip.cuh", "vd_internal.cuh"):
+    for f in ("vd_cells.cu", "vd_big.cuh", "vd_clip.cuh", "vd_internal.cuh"):
         hsh.update(open(os.path.join(ROOT, "paper_2605_06408_gb300", "csrc", f), "rb").read())
     return hsh.hexdigest()[:16]
 
