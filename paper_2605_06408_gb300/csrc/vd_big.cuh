@@ -803,15 +803,14 @@ __device__ inline void big_gc(BigCell& c, const BigArena& A) {
 
 static __device__ __noinline__ bool big_resolve64(const BigArena& A, uint64_t tri, int hpid, float4 me, const float* lo,
                                            const float* hi, const float4* __restrict__ sites, long long& amb) {
-  PlaneT<double> P0 = plane64(A.pid[bfield(tri, 0)], me, lo, hi, sites);
-  PlaneT<double> P1 = plane64(A.pid[bfield(tri, 1)], me, lo, hi, sites);
-  PlaneT<double> P2 = plane64(A.pid[bfield(tri, 2)], me, lo, hi, sites);
-  double x, y, z, e;
-  vertex3<double>(P0, P1, P2, x, y, z, e);
-  PlaneT<double> H = plane64(hpid, me, lo, hi, sites);
-  double s = side<double>(H, x, y, z);
-  if (ambiguous<double>(s, e, H.e)) amb++;
-  return s > 0.0;
+  const Plane64u P0 = plane64u(A.pid[bfield(tri, 0)], me, lo, hi, sites);
+  const Plane64u P1 = plane64u(A.pid[bfield(tri, 1)], me, lo, hi, sites);
+  const Plane64u P2 = plane64u(A.pid[bfield(tri, 2)], me, lo, hi, sites);
+  const Plane64u H = plane64u(hpid, me, lo, hi, sites);
+  bool a = false;
+  const bool out = side64u(P0, P1, P2, H, a);
+  if (a) amb++;
+  return out;
 }
 
 // Clip by plane H of site hpid (App. B), memory-resident form. `filtered`:

@@ -96,19 +96,126 @@ __device__ __forceinline__ PlaneT<double> plane64(int id, const float4& me, cons
   return box_plane<double>(-1 - id, me.x, me.y, me.z, lo, hi);
 }
 
+// ---------------------------------------------------------------- FP64 re-evaluation
+//
+// The FP64 steps take the planes unnormalised, n.x <= b with n = q - p and
+// b = (|n|^2 + w_p - w_q) / 2 (x in the frame of the site p; a box face has
+// a unit axis normal and b = hi - p or p - lo): the same half-spaces as the
+// normalised planes of Eq. 2, formed without a square root or a division.
+// The vertex of three planes is then one Cramer solve, x = num / W, and the
+// sign of a fourth plane H at that vertex is sign(W) sign(n_H.num - b_H W),
+// a polynomial in the inputs with no division at all. Each quantity carries
+// an a-priori bound on its rounding error, from the magnitudes below
+// (n1 = |n|_1, bm = |n|^2 + |w_p| + |w_q| bounds |b| and its error /4u):
+// every entry of n is off by at most u|n_i|, b by at most 4u bm.
+struct Plane64u {
+  double nx, ny, nz, b, n1, bm;
+};
+
+__device__ __forceinline__ Plane64u plane64u(int id, const float4& me, const float* lo, const float* hi,
+                                             const float4* __restrict__ sites) {
+  Plane64u P;
+  if (id >= 0) {
+    const float4 q = sites[id];
+    P.nx = (double)q.x - (double)me.x;
+    P.ny = (double)q.y - (double)me.y;
+    P.nz = (double)q.z - (double)me.z;
+    const double nn = fma(P.nx, P.nx, fma(P.ny, P.ny, P.nz * P.nz));
+    P.b = 0.5 * (nn + ((double)me.w - (double)q.w));
+    P.n1 = fabs(P.nx) + fabs(P.ny) + fabs(P.nz);
+    P.bm = nn + fabs((double)me.w) + fabs((double)q.w);
+  } else {
+    const int f = -1 - id, ax = f >> 1;
+    const double s = (f & 1) ? -1.0 : 1.0;
+    const double pc = ax == 0 ? (double)me.x : (ax == 1 ? (double)me.y : (double)me.z);
+    P.nx = ax == 0 ? s : 0.0;
+    P.ny = ax == 1 ? s : 0.0;
+    P.nz = ax == 2 ? s : 0.0;
+    const double bound = (f & 1) ? (double)lo[ax] : (double)hi[ax];
+    P.b = (f & 1) ? (pc - bound) : (bound - pc);
+    P.n1 = 1.0;
+    P.bm = fabs(pc) + fabs(bound);
+  }
+  return P;
+}
+
+// Cramer parts of the vertex of (A, B, C): num = b_A (n_B x n_C) + b_B (n_C x n_A)
+// + b_C (n_A x n_B), W = n_A.(n_B x n_C), with bounds dW on |W - W_exact| and
+// dnum on each |num_i - num_i,exact| (cross-product entries off by at most
+// 4u n1 n1 with the input errors, sums by 3u of their terms; the constants
+// are doubled).
+struct Cramer64 {
+  double nx, ny, nz, W, dW, dnum, mnum;
+};
+
+__device__ __forceinline__ Cramer64 cramer64(const Plane64u& A, const Plane64u& B, const Plane64u& C) {
+  const double u = Num<double>::u;
+  const double c1x = fma(B.ny, C.nz, -B.nz * C.ny), c1y = fma(B.nz, C.nx, -B.nx * C.nz),
+               c1z = fma(B.nx, C.ny, -B.ny * C.nx);
+  const double c2x = fma(C.ny, A.nz, -C.nz * A.ny), c2y = fma(C.nz, A.nx, -C.nx * A.nz),
+               c2z = fma(C.nx, A.ny, -C.ny * A.nx);
+  const double c3x = fma(A.ny, B.nz, -A.nz * B.ny), c3y = fma(A.nz, B.nx, -A.nx * B.nz),
+               c3z = fma(A.nx, B.ny, -A.ny * B.nx);
+  Cramer64 R;
+  R.W = fma(A.nx, c1x, fma(A.ny, c1y, A.nz * c1z));
+  R.nx = fma(A.b, c1x, fma(B.b, c2x, C.b * c3x));
+  R.ny = fma(A.b, c1y, fma(B.b, c2y, C.b * c3y));
+  R.nz = fma(A.b, c1z, fma(B.b, c2z, C.b * c3z));
+  const double bc = B.n1 * C.n1, ca = C.n1 * A.n1, ab = A.n1 * B.n1;
+  R.mnum = fabs(A.b) * bc + fabs(B.b) * ca + fabs(C.b) * ab;  // bounds every |num_i| term sum
+  R.dW = 16.0 * u * (A.n1 * bc);
+  R.dnum = 16.0 * u * R.mnum + 8.0 * u * (A.bm * bc + B.bm * ca + C.bm * ab);
+  return R;
+}
+
+// Vertex of (A, B, C) and a bound E on |x - x_exact|_1 (first order, with
+// |W| kept above 64 dW so that the second-order terms stay below a third of
+// it; E = inf otherwise).
+__device__ __forceinline__ void vertex64u(const Plane64u& A, const Plane64u& B, const Plane64u& C, double& x,
+                                          double& y, double& z, double& E) {
+  const double u = Num<double>::u;
+  const Cramer64 R = cramer64(A, B, C);
+  const double iw = 1.0 / R.W;
+  x = R.nx * iw;
+  y = R.ny * iw;
+  z = R.nz * iw;
+  const double x1 = fabs(x) + fabs(y) + fabs(z);
+  if (!(fabs(R.W) > 64.0 * R.dW) || !(x1 < 1e300)) {
+    E = INFINITY;
+  } else {
+    E = 1.5 * (3.0 * R.dnum + x1 * R.dW) / fabs(R.W) + 4.0 * u * x1;
+  }
+}
+
+// Does the vertex of (A, B, C) lie strictly outside H? D = n_H.num - b_H W has
+// the sign of (n_H.x - b_H) W; its error is at most dD (the errors of num and
+// W carried through, n_H and b_H off by u n1 and 4u bm, and the rounding of
+// the sums); amb is set when |D| <= dD or W's own sign is not certain, and
+// the FP64 sign is taken then.
+__device__ __forceinline__ bool side64u(const Plane64u& A, const Plane64u& B, const Plane64u& C, const Plane64u& H,
+                                        bool& amb) {
+  const double u = Num<double>::u;
+  const Cramer64 R = cramer64(A, B, C);
+  const double D = fma(H.nx, R.nx, fma(H.ny, R.ny, fma(H.nz, R.nz, -H.b * R.W)));
+  const double mW = A.n1 * B.n1 * C.n1;
+  const double dD = 2.0 * (H.n1 * (R.dnum + 4.0 * u * R.mnum) + fabs(H.b) * R.dW + 8.0 * u * H.bm * mW +
+                           4.0 * u * (H.n1 * R.mnum + fabs(H.b) * mW));
+  amb = !(fabs(R.W) > R.dW) || !(fabs(D) > dD);
+  return R.W > 0.0 ? D > 0.0 : D < 0.0;
+}
+
 // FP64 re-evaluation of "vertex tri lies outside the plane of site hpid".
 template <int VPL, int PCAP, int QPL>
 static __device__ __noinline__ bool resolve64(WarpSmem<VPL, PCAP, QPL>& S, uint32_t tri, int hpid, float4 me,
                                               const float* lo, const float* hi, const float4* __restrict__ sites) {
-  PlaneT<double> A = plane64(S.pid[tri & 255u], me, lo, hi, sites);
-  PlaneT<double> B = plane64(S.pid[(tri >> 8) & 255u], me, lo, hi, sites);
-  PlaneT<double> C = plane64(S.pid[(tri >> 16) & 255u], me, lo, hi, sites);
-  double x, y, z, e;
-  vertex3<double>(A, B, C, x, y, z, e);
-  PlaneT<double> H = plane64(hpid, me, lo, hi, sites);
-  double s = side<double>(H, x, y, z);
-  if (ambiguous<double>(s, e, H.e)) atomicAdd(&S.ct.fp64amb, 1u);
-  return s > 0.0;
+  const Plane64u A = plane64u(S.pid[tri & 255u], me, lo, hi, sites);
+  const Plane64u B = plane64u(S.pid[(tri >> 8) & 255u], me, lo, hi, sites);
+  const Plane64u C = plane64u(S.pid[(tri >> 16) & 255u], me, lo, hi, sites);
+  const Plane64u H = plane64u(hpid, me, lo, hi, sites);
+  bool amb = false;
+  const bool out = side64u(A, B, C, H, amb);
+  if (amb) atomicAdd(&S.ct.fp64amb, 1u);
+  return out;
 }
 
 // FP64 re-solve of the vertex of planes (pa, pb, ph) (plane ids: sorted
@@ -117,10 +224,10 @@ static __device__ __noinline__ bool resolve64(WarpSmem<VPL, PCAP, QPL>& S, uint3
 static __device__ __noinline__ void refine_vertex(int pa, int pb, int ph, float4 me, const float* lo, const float* hi,
                                            const float4* __restrict__ sites, float& x, float& y, float& z,
                                            float& e) {
-  PlaneT<double> A = plane64(pa, me, lo, hi, sites), B = plane64(pb, me, lo, hi, sites),
-                 H = plane64(ph, me, lo, hi, sites);
+  const Plane64u A = plane64u(pa, me, lo, hi, sites), B = plane64u(pb, me, lo, hi, sites),
+                 H = plane64u(ph, me, lo, hi, sites);
   double X, Y, Z, E;
-  vertex3<double>(A, B, H, X, Y, Z, E);
+  vertex64u(A, B, H, X, Y, Z, E);
   x = (float)X;
   y = (float)Y;
   z = (float)Z;
@@ -638,8 +745,8 @@ __device__ __forceinline__ void vertex64(uint32_t a, uint32_t b, uint32_t c, con
                                          const float* hi, const float4* __restrict__ sites, double& x, double& y,
                                          double& z) {
   double e;
-  vertex3<double>(plane64(pid[a], me, lo, hi, sites), plane64(pid[b], me, lo, hi, sites),
-                  plane64(pid[c], me, lo, hi, sites), x, y, z, e);
+  vertex64u(plane64u(pid[a], me, lo, hi, sites), plane64u(pid[b], me, lo, hi, sites),
+            plane64u(pid[c], me, lo, hi, sites), x, y, z, e);
 }
 
 // Volume and first moment about c of the register-path polytope gathered in

@@ -108,15 +108,14 @@ __device__ void t_init(TCell& C) {
 // FP64 re-evaluation of "vertex tri lies outside the plane of site hpid".
 static __device__ __noinline__ bool t_resolve64(const TCell& C, uint32_t tri, int hpid,
                                                 const float4* __restrict__ sites, long long& amb) {
-  const PlaneT<double> A = plane64(C.pid[tri & 255u], C.me, C.lo, C.hi, sites);
-  const PlaneT<double> B = plane64(C.pid[(tri >> 8) & 255u], C.me, C.lo, C.hi, sites);
-  const PlaneT<double> D = plane64(C.pid[(tri >> 16) & 255u], C.me, C.lo, C.hi, sites);
-  double x, y, z, e;
-  vertex3<double>(A, B, D, x, y, z, e);
-  const PlaneT<double> H = plane64(hpid, C.me, C.lo, C.hi, sites);
-  const double s = side<double>(H, x, y, z);
-  if (ambiguous<double>(s, e, H.e)) amb++;
-  return s > 0.0;
+  const Plane64u A = plane64u(C.pid[tri & 255u], C.me, C.lo, C.hi, sites);
+  const Plane64u B = plane64u(C.pid[(tri >> 8) & 255u], C.me, C.lo, C.hi, sites);
+  const Plane64u D = plane64u(C.pid[(tri >> 16) & 255u], C.me, C.lo, C.hi, sites);
+  const Plane64u H = plane64u(hpid, C.me, C.lo, C.hi, sites);
+  bool a = false;
+  const bool out = side64u(A, B, D, H, a);
+  if (a) amb++;
+  return out;
 }
 
 // Plane garbage collection (App. A.4): keep the planes the inside vertices
