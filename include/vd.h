@@ -410,6 +410,22 @@ int vd_autotune_batched(vd_ctx* ctx, const float* sites_xyz, const float* weight
 int vd_cells_noalloc(const float* sites_xyz, const float* weights, int64_t n, vd_box bbox, int32_t* counts,
                      int32_t* neighbors, float* volume, float* centroid, int32_t* status, void* stream);
 
+/* Copy `bytes` bytes from src to dst with a kernel on `stream` (no paper
+ * counterpart: the transfer of a build's inputs and outputs between the
+ * host and the GPU). Each pointer is DEVICE memory or page-locked HOST
+ * memory (cudaHostAlloc / cudaHostRegister, or a pinned PyTorch tensor): on
+ * a system with unified addressing such as the GB300's Grace host, the
+ * kernel's threads read and write host memory through the NVLink-C2C link
+ * directly. After a long kernel this runs at the link's rate, while a
+ * cudaMemcpyAsync on the copy engine of a freshly idle GPU ran at 10-50 GB/s
+ * for its first gigabytes. Any alignment and size are accepted (16-byte
+ * vectors where src and dst share their alignment modulo 16). The ranges
+ * must not overlap; the caller owns both buffers and keeps them alive until
+ * the copy has run. Returns VD_OK (bytes == 0 enqueues nothing),
+ * VD_ERR_INVALID_ARG (NULL pointer with bytes > 0, bytes < 0, or a pointer
+ * to pageable host memory, which the GPU cannot reach), VD_ERR_CUDA. */
+int vd_copy(void* dst, const void* src, int64_t bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libvd.so")
 SOURCES = ["vd_api.cu", "vd_bvh.cu", "vd_cells.cu", "vd_thread.cu", "vd_csr.cu", "vd_backward.cu", "vd_noalloc.cu",
-           "vd_knn.cu"]
+           "vd_knn.cu", "vd_copy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

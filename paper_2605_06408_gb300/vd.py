@@ -29,7 +29,7 @@ ABI_FUNCTIONS = (
     "vd_default_config", "vd_create", "vd_destroy", "vd_set_config", "vd_reserve", "vd_workspace_bytes",
     "vd_build", "vd_copy_neighbors", "vd_build_batched", "vd_backward", "vd_get_timings", "vd_get_status",
     "vd_error_string", "vd_cells_noalloc", "vd_autotune", "vd_autotune_batched", "vd_cells_mesh",
-    "vd_backward_mesh", "vd_ambiguous_cells", "vd_set_partition",
+    "vd_backward_mesh", "vd_ambiguous_cells", "vd_set_partition", "vd_copy",
 )
 VD_TUNE_FORCE = 1
 
@@ -140,6 +140,7 @@ def load_library(build_if_missing: bool = True):
                                             ctypes.POINTER(VdConfig), P]
         lib.vd_ambiguous_cells.argtypes = [P, P, I64, P]
         lib.vd_set_partition.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+        lib.vd_copy.argtypes = [P, P, I64, P]
         lib.vd_error_string.argtypes = [I]
         lib.vd_error_string.restype = ctypes.c_char_p
         for f in ABI_FUNCTIONS:
@@ -184,6 +185,27 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def _stream_ptr(device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def copy_(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """dst[...] = src through vd_copy: the library's SM copy between device
+    memory and page-locked host memory (either side; a CUDA tensor or a
+    pinned CPU tensor), on the current stream of the CUDA side's device.
+    Both tensors contiguous, of the same dtype and number of elements."""
+    if dst.dtype != src.dtype or dst.numel() != src.numel():
+        raise ValueError("copy_: dst and src differ in dtype or size")
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("copy_: tensors must be contiguous")
+    dev = dst.device if dst.is_cuda else src.device
+    if not dev.type == "cuda":
+        raise ValueError("copy_: one side must be a CUDA tensor")
+    for t in (dst, src):
+        if not t.is_cuda and not t.is_pinned():
+            raise ValueError("copy_: a CPU tensor must be pinned (page-locked)")
+    nbytes = dst.numel() * dst.element_size()
+    with torch.cuda.device(dev):
+        _check(load_library().vd_copy(_ptr(dst), _ptr(src), nbytes, _stream_ptr(dev)), "vd_copy")
+    return dst
 
 
 def _box(bbox) -> VdBox:

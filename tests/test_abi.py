@@ -47,6 +47,10 @@ def test_error_strings_and_null_arguments(lib):
     assert lib.vd_backward(None, None, None, None, None, 1, None) == vd.VD_ERR_INVALID_ARG
     assert lib.vd_create(None, 0, None) == vd.VD_ERR_INVALID_ARG
     assert lib.vd_get_status(None, None) == vd.VD_ERR_INVALID_ARG
+    # vd_copy rejects bad sizes and NULL pointers before any CUDA call
+    assert lib.vd_copy(None, None, 0, None) == vd.VD_OK
+    assert lib.vd_copy(None, None, 16, None) == vd.VD_ERR_INVALID_ARG
+    assert lib.vd_copy(None, None, -1, None) == vd.VD_ERR_INVALID_ARG
     cfg = vd.VdConfig()
     assert lib.vd_default_config(ctypes.byref(cfg)) == vd.VD_OK
     assert cfg.leaf_size == 16 and cfg.cull_mode == 0
