@@ -62,9 +62,15 @@ __device__ int process_leaf(Cell<VPL, PCAP, QPL>& c, WarpSmem<VPL, PCAP, QPL>& S
       for (int k = 0; k < kKnn; k++) act = act && S.knn[k] != j;
     }
   }
-  if (act) act = P.loser[j] == 0;
+  // the site and its duplicate-loser flag are loaded together (both
+  // indices are valid when act holds); a loser takes no part
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (act) q = P.sites[j];
+  unsigned char lost = 0;
+  if (act) {
+    lost = P.loser[j];
+    q = P.sites[j];
+  }
+  act = act && lost == 0;
   PlaneT<float> H;
   H.nx = H.ny = H.nz = H.b = H.e = 0.0f;
   bool keep = false, dup = false;
