@@ -38,7 +38,7 @@ struct Layout {
 
 int64_t ovf_capacity(int64_t n) { return n > 4096 ? n : 4096; }
 int64_t pool_capacity(int64_t n) { return n > (1 << 22) ? n : (1 << 22); }
-int big_warps(int num_sms) { return num_sms * kBigWarpsPerBlock; }
+int big_warps(int num_sms) { return num_sms * kBigBlocksPerSm * kBigWarpsPerBlock; }
 
 }  // namespace
 

@@ -1018,7 +1018,7 @@ __device__ bool big_build_cell(const CellBuffers& P, const BigArena& A, int si, 
 }
 
 template <bool GEN>
-__global__ void big_cells_kernel(CellBuffers P) {
+__global__ void __launch_bounds__(32 * kBigWarpsPerBlock, kBigBlocksPerSm) big_cells_kernel(CellBuffers P) {
   const unsigned lane = lane_id();
   const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   BigArena A = big_arena(P.arena, slot);
@@ -1107,7 +1107,7 @@ cudaError_t launch_cells(const CellBuffers& c, int num_sms, cudaStream_t s, cons
                                                                                                 : big_cells_kernel<false>;
   err = cudaFuncSetAttribute(big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_smem);
   if (err != cudaSuccess) return err;
-  big<<<num_sms, 32 * kBigWarpsPerBlock, big_smem, s>>>(c);
+  big<<<num_sms * kBigBlocksPerSm, 32 * kBigWarpsPerBlock, big_smem, s>>>(c);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kMaxLeaf = 32;            // leaf sizes 1..32 (one site per lane)
 constexpr int kMaxSites = 1 << 26;      // leaf refs pack the first site in 26 bits
 constexpr int kMaxSets = 1024;
-constexpr int kBigWarpsPerBlock = 8;  // large-cell path: one block of this many warps per SM
+constexpr int kBigWarpsPerBlock = 8;  // large-cell path: blocks of this many warps,
+constexpr int kBigBlocksPerSm = 2;     // this many per SM (one arena per warp)
 constexpr uint32_t kEmptyTri = 0xffffffffu;
 #ifndef VD_KNN
 #define VD_KNN 8
